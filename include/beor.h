@@ -1,0 +1,193 @@
+/*
+ * beor.h -- C ABI of the GB300 BayesEoR likelihood library.
+ *
+ * The library evaluates, for batches of prior points phi, the marginal
+ * likelihood of the joint EoR + foreground linear model that the paper's
+ * sampler explores (Sec. "Statement of need": the amplitudes are marginalised
+ * so that the power spectrum is sampled directly from its marginal posterior;
+ * Eq. for P(k_i): one power amplitude per spherical k shell):
+ *
+ *     Sigma(phi) = T^H N^-1 T + Phi(phi)^-1,     dbar = T^H N^-1 d
+ *     abar       = Sigma^-1 dbar
+ *     lnL(phi)   = -1/2 log|Phi| - 1/2 log|Sigma| + 1/2 dbar^H Sigma^-1 dbar
+ *
+ * T is the instrument forward model (Sec. "Running BayesEoR": primary beam
+ * and uv sampling of each baseline), N the diagonal noise covariance and
+ * Phi the diagonal prior.  EoR model amplitude j in k bin kbin[j] has prior
+ * variance 10^phi[kbin[j]]; foreground (LSSM) amplitudes, kbin[j] == -1, have
+ * the fixed variance lssm_prior_var.
+ *
+ * Conventions for every call:
+ *  - Return value: BEOR_OK or a negative BEOR_E* code.  After BEOR_ECUDA or
+ *    BEOR_ETIMEOUT the context is poisoned and later calls return
+ *    BEOR_ESTATE.  beor_strerror() names a code.
+ *  - Ownership: the caller owns every buffer it passes.  Inputs are copied
+ *    (host or device memory, detected per pointer) before the call returns
+ *    or, for stream-ordered calls, before the work enqueued on the stream
+ *    reads them; no caller pointer is retained.  Output buffers may be host
+ *    or device memory.  Host outputs are written when the call returns
+ *    (the call synchronises the stream); device outputs are valid once the
+ *    given stream reaches the end of the enqueued work.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *  - Order: a model (beor_set_T or beor_set_instrument), then beor_set_data,
+ *    then beor_precompute, then beor_lnl / beor_lnl_multi /
+ *    beor_posterior_mean; otherwise BEOR_ESTATE.
+ *  - Threads: one context must not be used by two threads at once.
+ *  - Complex numbers are beor_c128 {re, im} pairs (same layout as
+ *    std::complex<double> / numpy complex128); matrices are row-major.
+ *  - Per-point status: 0 = ok; j > 0 = Sigma not positive definite at
+ *    1-based column j (lnL = -inf); -1 = iterative refinement of the solve
+ *    did not reach its tolerance (lnL still returned).
+ */
+#ifndef BEOR_H
+#define BEOR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct beor_ctx beor_ctx;
+typedef struct { double re, im; } beor_c128;
+
+enum {
+  BEOR_OK = 0,
+  BEOR_EINVAL = -1,    /* bad argument (size, pointer, value) */
+  BEOR_ENOMEM = -2,    /* device or host allocation failed */
+  BEOR_ECUDA = -3,     /* a CUDA call or kernel failed */
+  BEOR_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
+  BEOR_ESTATE = -5,    /* call out of order, or context poisoned */
+  BEOR_ENOTSUP = -6    /* feature not available on this device */
+};
+
+enum { BEOR_PREC_FP64 = 0, BEOR_PREC_MIXED = 1 };
+
+/* Create a context on CUDA device `device`.
+ * precision = BEOR_PREC_FP64: every step in IEEE float64 (the comparator).
+ * precision = BEOR_PREC_MIXED: trailing and panel updates of the blocked
+ *   Cholesky run as exact bf16 slice products on the tensor cores with fp32
+ *   accumulation, the working matrix is kept as a pair of fp32 words per
+ *   real number, diagonal blocks and log-determinants in float64, and the
+ *   solve is refined against the float64 precompute. */
+int beor_create(beor_ctx **out, int device, int precision);
+int beor_destroy(beor_ctx *ctx);
+
+/* Dense instrument model (Sec. "Running BayesEoR"; T maps model amplitudes
+ * to visibilities).  T: n_vis x n_model complex, row-major with leading
+ * dimension ld >= n_model, host or device.  kbin: n_model int32 in
+ * [-1, n_k); -1 marks a foreground amplitude.  n_k >= 1.
+ * lssm_prior_var > 0.  Errors: BEOR_EINVAL for sizes <= 0, a kbin value
+ * out of range or an empty k bin. */
+int beor_set_T(beor_ctx *ctx, const beor_c128 *T, int64_t n_vis, int64_t n_model,
+               int64_t ld, const int32_t *kbin, int n_k, double lssm_prior_var);
+
+/* Factored instrument model: T[(f,tb),(c,x)] = A[f][tb][c] * W[f][x], the
+ * per-frequency response of each baseline/time to each uv cell times the
+ * spectral basis (eta modes and foreground spectra) of each model column.
+ * A: nf x ntb x ncells complex (row-major), W: nf x nx complex; the model
+ * index is j = c*nx + x and the visibility index (f*ntb + tb).  The
+ * precompute then never forms T.  Same kbin / n_k / lssm_prior_var rules as
+ * beor_set_T with n_model = ncells*nx. */
+int beor_set_instrument(beor_ctx *ctx, const beor_c128 *A, const beor_c128 *W, int nf,
+                        int64_t ntb, int ncells, int nx, const int32_t *kbin, int n_k,
+                        double lssm_prior_var);
+
+/* Data vector d (n_vis complex) and noise variances (n_vis, all > 0): the
+ * diagonal of N.  Host or device. */
+int beor_set_data(beor_ctx *ctx, const beor_c128 *d, const double *noise_var);
+
+/* One-off precompute of M = T^H N^-1 T (float64, Hermitian, lower triangle
+ * authoritative) and dbar = T^H N^-1 d, enqueued on `stream` and completed
+ * before return. */
+int beor_precompute(beor_ctx *ctx, void *stream);
+
+/* lnL for B prior points.  phi: B x n_k float64, row-major, log10 power
+ * amplitudes (host or device).  lnl_out: B float64, status_out: B int32
+ * (host or device).  The whole batch is factorised together; the call
+ * returns after the results are written. */
+int beor_lnl(beor_ctx *ctx, const double *phi, int B, double *lnl_out, int32_t *status_out,
+             void *stream);
+
+/* Batched evaluation across several contexts (e.g. sub-band problems of
+ * uneven model dimension), all on one device with one precision: set s
+ * evaluates B[s] points phi[s] (B[s] x n_k[s]) into lnl_out[s], status_out[s].
+ * One batched factorisation covers every problem of every set. */
+int beor_lnl_multi(beor_ctx *const *ctxs, int n_sets, const double *const *phi, const int *B,
+                   double *const *lnl_out, int32_t *const *status_out, void *stream);
+
+/* Posterior mean (maximum-a-posteriori amplitudes) abar = Sigma^-1 dbar for
+ * one prior point phi (n_k).  abar_out: n_model complex (host or device). */
+int beor_posterior_mean(beor_ctx *ctx, const double *phi, beor_c128 *abar_out,
+                        int32_t *status_out, void *stream);
+
+int beor_get_model_dims(const beor_ctx *ctx, int64_t *n_vis, int64_t *n_model, int *n_k);
+
+/* Copies of the precompute for inspection: M (n_model x n_model, full
+ * Hermitian, row-major) and dbar (n_model).  Host or device output. */
+int beor_get_M(beor_ctx *ctx, beor_c128 *M_out);
+int beor_get_dbar(beor_ctx *ctx, beor_c128 *dbar_out);
+
+/* Diagnostics of the last lnL / posterior-mean call on this context. */
+typedef struct {
+  int refine_iters_max;     /* largest number of refinement steps taken */
+  double resid_rel_max;     /* largest final ||dbar - Sigma x|| / ||dbar|| */
+  double ms_last;           /* device time of the last batched evaluation */
+  int64_t kernel_launches;  /* kernels launched by the last batched evaluation */
+} beor_stats;
+int beor_get_stats(const beor_ctx *ctx, beor_stats *out);
+
+/* Per-point log-determinant pieces of the last beor_lnl call on ctx (B
+ * values each, host memory): log|Phi|, log|Sigma| and q = dbar^H abar. */
+int beor_get_terms(const beor_ctx *ctx, double *logdet_phi, double *logdet_sigma, double *q,
+                   int B);
+
+/* ---------------------------------------------------------------------
+ * Learned emulator of lnL(phi) (pre-screening for the nested sampler).
+ * A multilayer perceptron n_in -> depth x width GELU -> 1 with bf16 weights
+ * and activations, fp32 accumulation and fp32 master weights / Adam state,
+ * trained and evaluated by the library's own kernels.
+ * ------------------------------------------------------------------- */
+typedef struct beor_mlp beor_mlp;
+
+/* Create on `device`; weights drawn from a counter-based generator seeded
+ * by `seed` (He-uniform).  width must be a multiple of 16, 16 <= width <=
+ * 256, 1 <= depth <= 8, 1 <= n_in <= 16. */
+int beor_mlp_create(beor_mlp **out, int device, int n_in, int width, int depth, uint64_t seed);
+int beor_mlp_destroy(beor_mlp *mlp);
+
+/* Input / target normalisation applied inside the network:
+ * x_used = (x - x_shift) * x_scale per input, y = y_net * y_scale + y_shift. */
+int beor_mlp_set_norm(beor_mlp *mlp, const float *x_shift, const float *x_scale, float y_shift,
+                      float y_scale);
+
+/* One Adam step (beta1, beta2, eps given) on a minibatch: x n x n_in float32,
+ * y n float32 (host or device).  loss_out (host, may be NULL): mean squared
+ * error of the minibatch before the step, in normalised units. */
+int beor_mlp_train_step(beor_mlp *mlp, const float *x, const float *y, int n, float lr,
+                        float beta1, float beta2, float eps, float *loss_out, void *stream);
+
+/* Predictions for n points (x: n x n_in float32, y_out: n float32; host or
+ * device). */
+int beor_mlp_infer(beor_mlp *mlp, const float *x, int n, float *y_out, void *stream);
+
+/* Parameter access (fp32 master copy) for checking against the oracle:
+ * layer l (0..depth) weights W_l (out x in, row-major) and biases b_l.
+ * Sizes: layer 0 is width x n_in, hidden layers width x width, the last
+ * 1 x width. */
+int beor_mlp_get_params(beor_mlp *mlp, int layer, float *W, float *b);
+int beor_mlp_set_params(beor_mlp *mlp, int layer, const float *W, const float *b);
+
+/* Gradients (fp32) of the mean squared loss of one batch with respect to
+ * every parameter, written into the caller's buffers in the same layout as
+ * beor_mlp_get_params, without updating the weights. */
+int beor_mlp_grad(beor_mlp *mlp, const float *x, const float *y, int n, int layer, float *dW,
+                  float *db, float *loss_out);
+
+const char *beor_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEOR_H */
