@@ -1,0 +1,305 @@
+"""ctypes binding of the C ABI in include/beor.h (argument marshalling only).
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA); the
+library detects device pointers itself.  Streams default to torch's current
+CUDA stream when torch has initialised CUDA, else the legacy default stream.
+There is no fallback: without the compiled library every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbeor.so")
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+
+_c = ctypes
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+
+
+class BeorError(RuntimeError):
+    pass
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "or python -m paper_2501_12928_gb300._build")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "beor_create": [_c.POINTER(_P), _c.c_int, _c.c_int],
+        "beor_destroy": [_P],
+        "beor_set_T": [_P, _P, _I64, _I64, _I64, _P, _c.c_int, _c.c_double],
+        "beor_set_instrument": [_P, _P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _P, _c.c_int, _c.c_double],
+        "beor_set_data": [_P, _P, _P],
+        "beor_precompute": [_P, _P],
+        "beor_lnl": [_P, _P, _c.c_int, _P, _P, _P],
+        "beor_lnl_multi": [_P, _c.c_int, _P, _P, _P, _P, _P],
+        "beor_posterior_mean": [_P, _P, _P, _P, _P],
+        "beor_get_model_dims": [_P, _c.POINTER(_I64), _c.POINTER(_I64), _c.POINTER(_c.c_int)],
+        "beor_get_M": [_P, _P],
+        "beor_get_dbar": [_P, _P],
+        "beor_get_stats": [_P, _P],
+        "beor_get_terms": [_P, _P, _P, _P, _c.c_int],
+        "beor_mlp_create": [_c.POINTER(_P), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64],
+        "beor_mlp_destroy": [_P],
+        "beor_mlp_set_norm": [_P, _P, _P, _c.c_float, _c.c_float],
+        "beor_mlp_train_step": [_P, _P, _P, _c.c_int, _c.c_float, _c.c_float, _c.c_float, _c.c_float, _P, _P],
+        "beor_mlp_infer": [_P, _P, _c.c_int, _P, _P],
+        "beor_mlp_get_params": [_P, _c.c_int, _P, _P],
+        "beor_mlp_set_params": [_P, _c.c_int, _P, _P],
+        "beor_mlp_grad": [_P, _P, _P, _c.c_int, _c.c_int, _P, _P, _P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = _c.c_int
+    L.beor_strerror.argtypes = [_c.c_int]
+    L.beor_strerror.restype = _c.c_char_p
+    return L
+
+
+lib = None
+
+
+def _lib():
+    global lib
+    if lib is None:
+        lib = _load()
+    return lib
+
+
+def _check(code, what):
+    if code != 0:
+        msg = _lib().beor_strerror(code).decode()
+        raise BeorError(f"{what}: {msg} ({code})")
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("refine_iters_max", ctypes.c_int), ("resid_rel_max", ctypes.c_double),
+                ("ms_last", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _ptr(a, dtype, keep):
+    """Pointer to a contiguous array of `dtype` (numpy or torch); keeps it alive in `keep`."""
+    if hasattr(a, "data_ptr"):       # torch tensor
+        import torch
+        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.int32: torch.int32,
+               np.complex128: torch.complex128}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            a = a.to(tdt).contiguous()
+        keep.append(a)
+        return ctypes.c_void_p(a.data_ptr())
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    keep.append(arr)
+    return ctypes.c_void_p(arr.ctypes.data)
+
+
+class Likelihood:
+    """One instrument: model, data, precompute and batched lnL evaluations."""
+
+    def __init__(self, precision: str | int = "fp64", device: int = 0):
+        prec = {"fp64": PREC_FP64, "mixed": PREC_MIXED}.get(precision, precision)
+        h = ctypes.c_void_p()
+        _check(_lib().beor_create(ctypes.byref(h), device, int(prec)), "beor_create")
+        self._h = h
+        self.precision = prec
+        self.n_k = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().beor_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_T(self, T, kbin, n_k: int, lssm_prior_var: float):
+        keep = []
+        n_vis, n = T.shape
+        _check(_lib().beor_set_T(self._h, _ptr(T, np.complex128, keep), n_vis, n, n,
+                                 _ptr(kbin, np.int32, keep), n_k, float(lssm_prior_var)), "beor_set_T")
+        self.n_k = n_k
+
+    def set_instrument(self, A, W, kbin, n_k: int, lssm_prior_var: float):
+        keep = []
+        nf, ntb, ncells = A.shape
+        nx = W.shape[1]
+        _check(_lib().beor_set_instrument(self._h, _ptr(A, np.complex128, keep), _ptr(W, np.complex128, keep),
+                                          nf, ntb, ncells, nx, _ptr(kbin, np.int32, keep), n_k,
+                                          float(lssm_prior_var)), "beor_set_instrument")
+        self.n_k = n_k
+
+    def set_data(self, d, noise_var):
+        keep = []
+        _check(_lib().beor_set_data(self._h, _ptr(d, np.complex128, keep), _ptr(noise_var, np.float64, keep)),
+               "beor_set_data")
+
+    def precompute(self, stream=None):
+        _check(_lib().beor_precompute(self._h, _stream(stream)), "beor_precompute")
+
+    def dims(self):
+        nv, nm, nk = _I64(), _I64(), ctypes.c_int()
+        _check(_lib().beor_get_model_dims(self._h, ctypes.byref(nv), ctypes.byref(nm), ctypes.byref(nk)), "dims")
+        return nv.value, nm.value, nk.value
+
+    def lnl(self, phi, stream=None, out=None, status=None):
+        """lnL for a batch phi (B x n_k).  Returns (lnl[B], status[B]) as numpy
+        arrays, or fills the given output arrays/tensors."""
+        keep = []
+        phi2 = phi if hasattr(phi, "data_ptr") else np.atleast_2d(np.asarray(phi, dtype=np.float64))
+        B = phi2.shape[0]
+        o = np.empty(B, np.float64) if out is None else out
+        s = np.empty(B, np.int32) if status is None else status
+        _check(_lib().beor_lnl(self._h, _ptr(phi2, np.float64, keep), B, _ptr(o, np.float64, keep),
+                               _ptr(s, np.int32, keep), _stream(stream)), "beor_lnl")
+        if out is None and isinstance(keep[1], np.ndarray):
+            o = keep[1]
+        if status is None and isinstance(keep[2], np.ndarray):
+            s = keep[2]
+        return o, s
+
+    def posterior_mean(self, phi, stream=None):
+        keep = []
+        n = self.dims()[1]
+        a = np.empty(n, np.complex128)
+        st = np.zeros(1, np.int32)
+        _check(_lib().beor_posterior_mean(self._h, _ptr(np.asarray(phi, np.float64), np.float64, keep),
+                                          ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(st.ctypes.data),
+                                          _stream(stream)), "beor_posterior_mean")
+        return a, int(st[0])
+
+    def get_M(self):
+        n = self.dims()[1]
+        M = np.empty((n, n), np.complex128)
+        _check(_lib().beor_get_M(self._h, ctypes.c_void_p(M.ctypes.data)), "beor_get_M")
+        return M
+
+    def get_dbar(self):
+        n = self.dims()[1]
+        v = np.empty(n, np.complex128)
+        _check(_lib().beor_get_dbar(self._h, ctypes.c_void_p(v.ctypes.data)), "beor_get_dbar")
+        return v
+
+    def stats(self) -> dict:
+        st = _Stats()
+        _check(_lib().beor_get_stats(self._h, ctypes.byref(st)), "beor_get_stats")
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def terms(self, B: int):
+        a, b, c = (np.empty(B, np.float64) for _ in range(3))
+        _check(_lib().beor_get_terms(self._h, ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(b.ctypes.data),
+                                     ctypes.c_void_p(c.ctypes.data), B), "beor_get_terms")
+        return {"logdet_phi": a, "logdet_sigma": b, "q": c}
+
+
+def lnl_multi(likes: list, phis: list, stream=None):
+    """One batched evaluation over several instruments (uneven sizes allowed)."""
+    n = len(likes)
+    keep = []
+    ctxs = (ctypes.c_void_p * n)(*[lk._h.value for lk in likes])
+    phi_arr = [np.atleast_2d(np.asarray(p, np.float64)) for p in phis]
+    Bs = (ctypes.c_int * n)(*[p.shape[0] for p in phi_arr])
+    pp = (ctypes.c_void_p * n)(*[_ptr(p, np.float64, keep).value for p in phi_arr])
+    outs = [np.empty(p.shape[0], np.float64) for p in phi_arr]
+    sts = [np.empty(p.shape[0], np.int32) for p in phi_arr]
+    op = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+    sp = (ctypes.c_void_p * n)(*[s.ctypes.data for s in sts])
+    _check(_lib().beor_lnl_multi(ctypes.cast(ctxs, ctypes.c_void_p), n, ctypes.cast(pp, ctypes.c_void_p),
+                                 ctypes.cast(Bs, ctypes.c_void_p), ctypes.cast(op, ctypes.c_void_p),
+                                 ctypes.cast(sp, ctypes.c_void_p), _stream(stream)), "beor_lnl_multi")
+    return outs, sts
+
+
+class Emulator:
+    """MLP emulator of lnL(phi), trained and evaluated by the library's kernels."""
+
+    def __init__(self, n_in: int, width: int = 256, depth: int = 4, seed: int = 4, device: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib().beor_mlp_create(ctypes.byref(h), device, n_in, width, depth, seed), "beor_mlp_create")
+        self._h = h
+        self.n_in, self.width, self.depth = n_in, width, depth
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().beor_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_norm(self, x_shift, x_scale, y_shift: float, y_scale: float):
+        keep = []
+        _check(_lib().beor_mlp_set_norm(self._h, _ptr(x_shift, np.float32, keep), _ptr(x_scale, np.float32, keep),
+                                        float(y_shift), float(y_scale)), "beor_mlp_set_norm")
+
+    def train_step(self, x, y, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> float:
+        keep = []
+        loss = ctypes.c_float(0.0)
+        n = x.shape[0]
+        _check(_lib().beor_mlp_train_step(self._h, _ptr(x, np.float32, keep), _ptr(y, np.float32, keep), n,
+                                          lr, beta1, beta2, eps, ctypes.byref(loss), _stream(stream)),
+               "beor_mlp_train_step")
+        return loss.value
+
+    def infer(self, x, stream=None, out=None):
+        keep = []
+        n = x.shape[0]
+        y = np.empty(n, np.float32) if out is None else out
+        _check(_lib().beor_mlp_infer(self._h, _ptr(x, np.float32, keep), n, _ptr(y, np.float32, keep),
+                                     _stream(stream)), "beor_mlp_infer")
+        return keep[1] if out is None else out
+
+    def layer_shape(self, layer: int):
+        fan_in = self.n_in if layer == 0 else self.width
+        fan_out = 1 if layer == self.depth else self.width
+        return fan_out, fan_in
+
+    def get_params(self, layer: int):
+        o, i = self.layer_shape(layer)
+        W = np.empty((o, i), np.float32)
+        b = np.empty(o, np.float32)
+        _check(_lib().beor_mlp_get_params(self._h, layer, ctypes.c_void_p(W.ctypes.data),
+                                          ctypes.c_void_p(b.ctypes.data)), "beor_mlp_get_params")
+        return W, b
+
+    def set_params(self, layer: int, W, b):
+        keep = []
+        _check(_lib().beor_mlp_set_params(self._h, layer, _ptr(W, np.float32, keep), _ptr(b, np.float32, keep)),
+               "beor_mlp_set_params")
+
+    def grad(self, x, y, layer: int):
+        keep = []
+        o, i = self.layer_shape(layer)
+        dW = np.empty((o, i), np.float32)
+        db = np.empty(o, np.float32)
+        loss = ctypes.c_float(0.0)
+        _check(_lib().beor_mlp_grad(self._h, _ptr(x, np.float32, keep), _ptr(y, np.float32, keep), x.shape[0], layer,
+                                    ctypes.c_void_p(dW.ctypes.data), ctypes.c_void_p(db.ctypes.data),
+                                    ctypes.byref(loss)), "beor_mlp_grad")
+        return dW, db, loss.value

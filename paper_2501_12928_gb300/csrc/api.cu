@@ -1,0 +1,683 @@
+// C ABI of the library: contexts (one instrument each), the precompute, and
+// batched likelihood evaluations driven through captured CUDA graphs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "../../include/beor.h"
+#include "beor_common.cuh"
+#include "beor_internal.h"
+
+using namespace beor;
+
+namespace {
+
+constexpr int kRefineIters = 2;   // refinement steps of the mixed solve (fixed: graph-captured)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// copy n bytes from a host-or-device source to device memory
+cudaError_t to_device(void* dst, const void* src, size_t n, cudaStream_t s) {
+  return cudaMemcpyAsync(dst, src, n, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+}
+cudaError_t from_device(void* dst, const void* src, size_t n, cudaStream_t s) {
+  return cudaMemcpyAsync(dst, src, n, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t alloc(size_t bytes) {
+    release();
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    n = bytes;
+    return cudaSuccess;
+  }
+  template <typename T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct Plan;
+
+}  // namespace
+
+struct beor_ctx {
+  int device = 0;
+  int precision = BEOR_PREC_FP64;
+  bool poisoned = false;
+  // model
+  int model_kind = 0;   // 0 none, 1 dense T, 2 factored
+  int64_t n_vis = 0;
+  int n = 0, nt = 0, n_k = 0;
+  double lssm_prior_var = 1.0;
+  int nf = 0, ncells = 0, nx = 0;
+  int64_t ntb = 0, ld = 0;
+  DevBuf T, A, W, kbin;
+  // data
+  bool have_data = false;
+  DevBuf d, w;
+  // precompute
+  bool have_pre = false;
+  DevBuf M, dbar;
+  // bookkeeping
+  beor_stats stats{};
+  Plan* last_plan = nullptr;
+  int last_first = 0;
+  std::vector<double> last_ldphi, last_ldsig, last_q;
+};
+
+namespace {
+
+std::mutex g_mu;
+std::vector<Plan*> g_plans;
+
+struct Plan {
+  std::vector<beor_ctx*> ctxs;
+  std::vector<int> Bs;
+  int device = 0;
+  bool mixed = false;
+  int P = 0, max_nt = 0;
+  int64_t rows = 0;
+  std::vector<Prob> h_prob;
+  std::vector<SetDesc> h_sets;
+  std::vector<int> first;   // first problem index of each set
+  DevBuf d_prob, d_sets, ws, dinv, phi_inv, vecs, scal, flags, phis, panel_sl, panel_exp, linv_sl, linv_exp;
+  std::vector<int64_t> phi_off;
+  BatchView view{};
+  MixedMaps* maps = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int64_t launches = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  ~Plan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (maps) mixed_maps_destroy(maps);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+};
+
+int fail_cuda(beor_ctx* c, cudaError_t e) {
+  if (e == cudaSuccess) return BEOR_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return BEOR_ENOMEM;
+  }
+  if (c) c->poisoned = true;
+  return BEOR_ECUDA;
+}
+
+#define CKC(ctx, expr)                              \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) return fail_cuda(ctx, _e); \
+  } while (0)
+
+// The sequence of kernels of one batched evaluation.
+cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch) {
+  const BatchView& v = pl.view;
+  int64_t L = 0;
+  cudaError_t e;
+#define RUN(x)                      \
+  do {                              \
+    e = (x);                        \
+    if (e != cudaSuccess) return e; \
+  } while (0)
+  RUN(launch_prior_init(v, pl.mixed, s));
+  L += 2;
+  RUN(launch_copy_dbar(v, s));
+  L += 1;
+  for (int k = 0; k < pl.max_nt; ++k) {
+    RUN(launch_diag(v, k, pl.mixed, s));
+    L += 1;
+    if (k + 1 < pl.max_nt) {
+      if (pl.mixed) {
+        RUN(launch_slice_panel(v, k, s));
+        RUN(launch_panel_mixed(v, pl.maps, k, s));
+        RUN(launch_slice_panel(v, k, s));
+        RUN(launch_trail_mixed(v, pl.maps, k, s));
+        L += 4;
+      } else {
+        RUN(launch_panel_f64(v, k, s));
+        RUN(launch_trail_f64(v, k, s));
+        L += 2;
+      }
+    }
+  }
+  RUN(launch_solve(v, pl.mixed, v.vec_b, v.vec_x, s));
+  L += 1;
+  if (pl.mixed) {
+    for (int it = 0; it < kRefineIters; ++it) {
+      RUN(launch_residual(v, s));
+      RUN(launch_solve(v, true, v.vec_r, v.vec_d, s));
+      RUN(launch_refine_update(v, s));
+      L += 3;
+    }
+    RUN(launch_residual(v, s));
+    L += 1;
+  }
+  RUN(launch_lnl(v, s));
+  L += 1;
+#undef RUN
+  if (nlaunch) *nlaunch = L;
+  return cudaSuccess;
+}
+
+int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, Plan** out) {
+  Plan* pl = new Plan();
+  pl->device = ctxs[0]->device;
+  pl->mixed = ctxs[0]->precision == BEOR_PREC_MIXED;
+  int64_t ws_elems = 0, dinv_elems = 0, rows = 0;
+  int64_t phi_total = 0;
+  for (int s = 0; s < nsets; ++s) {
+    beor_ctx* c = ctxs[s];
+    pl->ctxs.push_back(c);
+    pl->Bs.push_back(Bs[s]);
+    pl->first.push_back((int)pl->h_prob.size());
+    SetDesc sd{};
+    sd.n = c->n;
+    sd.nt = c->nt;
+    sd.n_k = c->n_k;
+    sd.lssm_prior_var = c->lssm_prior_var;
+    sd.M = c->M.as<double2>();
+    sd.dbar = c->dbar.as<double2>();
+    sd.kbin = c->kbin.as<int32_t>();
+    pl->phi_off.push_back(phi_total);
+    phi_total += (int64_t)Bs[s] * c->n_k;
+    pl->h_sets.push_back(sd);
+    for (int b = 0; b < Bs[s]; ++b) {
+      Prob pr{};
+      pr.n = c->n;
+      pr.nt = c->nt;
+      pr.set = s;
+      pr.b = b;
+      pr.ws_off = ws_elems;
+      pr.dinv_off = dinv_elems;
+      pr.row_off = rows;
+      ws_elems += tri_count(c->nt) * BEOR_TILE_ELEMS;
+      dinv_elems += (int64_t)c->nt * (BEOR_TB * (BEOR_TB + 1) / 2);
+      rows += (int64_t)c->nt * BEOR_TB;
+      pl->max_nt = std::max(pl->max_nt, c->nt);
+      pl->h_prob.push_back(pr);
+    }
+  }
+  pl->P = (int)pl->h_prob.size();
+  pl->rows = rows;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (x != cudaSuccess && e == cudaSuccess) e = x;
+  };
+  chk(pl->phis.alloc(sizeof(double) * std::max<int64_t>(1, phi_total)));
+  for (int s = 0; s < nsets; ++s) pl->h_sets[s].phi = pl->phis.as<double>() + pl->phi_off[s];
+  chk(pl->d_prob.alloc(sizeof(Prob) * pl->P));
+  chk(pl->d_sets.alloc(sizeof(SetDesc) * nsets));
+  chk(pl->ws.alloc((pl->mixed ? sizeof(float4) : sizeof(double2)) * (size_t)ws_elems));
+  chk(pl->dinv.alloc(sizeof(double2) * (size_t)dinv_elems));
+  chk(pl->phi_inv.alloc(sizeof(double) * (size_t)rows));
+  chk(pl->vecs.alloc(sizeof(double2) * (size_t)rows * 6));
+  chk(pl->scal.alloc(sizeof(double) * (size_t)pl->P * 6 + sizeof(int32_t) * pl->P));
+  chk(pl->flags.alloc(sizeof(Flags)));
+  if (pl->mixed) {
+    chk(pl->panel_sl.alloc(sizeof(__nv_bfloat16) * (size_t)BEOR_NPLANE * rows * BEOR_TB));
+    chk(pl->panel_exp.alloc(sizeof(int32_t) * (size_t)rows));
+    chk(pl->linv_sl.alloc(sizeof(__nv_bfloat16) * (size_t)BEOR_NPLANE * pl->P * BEOR_TB * BEOR_TB));
+    chk(pl->linv_exp.alloc(sizeof(int32_t) * (size_t)pl->P * BEOR_TB));
+  }
+  if (e != cudaSuccess) {
+    delete pl;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? BEOR_ENOMEM : BEOR_ECUDA;
+  }
+  chk(cudaMemcpy(pl->d_prob.p, pl->h_prob.data(), sizeof(Prob) * pl->P, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(pl->d_sets.p, pl->h_sets.data(), sizeof(SetDesc) * nsets, cudaMemcpyHostToDevice));
+  chk(cudaMemset(pl->flags.p, 0, sizeof(Flags)));
+  BatchView& v = pl->view;
+  v.P = pl->P;
+  v.nsets = nsets;
+  v.prob = pl->d_prob.as<Prob>();
+  v.sets = pl->d_sets.as<SetDesc>();
+  v.max_nt = pl->max_nt;
+  v.ws = pl->ws.p;
+  v.dinv = pl->dinv.as<double2>();
+  v.phi_inv = pl->phi_inv.as<double>();
+  double2* vb = pl->vecs.as<double2>();
+  v.vec_b = vb;
+  v.vec_y = vb + rows;
+  v.vec_x = vb + 2 * rows;
+  v.vec_t = vb + 3 * rows;
+  v.vec_r = vb + 4 * rows;
+  v.vec_d = vb + 5 * rows;
+  double* sc = pl->scal.as<double>();
+  v.logdet_phi = sc;
+  v.logdet_sigma = sc + pl->P;
+  v.q = sc + 2 * pl->P;
+  v.lnl = sc + 3 * pl->P;
+  v.resid = sc + 4 * pl->P;
+  v.status = reinterpret_cast<int32_t*>(sc + 6 * pl->P);
+  v.flags = pl->flags.as<Flags>();
+  v.panel_sl = pl->panel_sl.as<__nv_bfloat16>();
+  v.panel_exp = pl->panel_exp.as<int32_t>();
+  v.linv_sl = pl->linv_sl.as<__nv_bfloat16>();
+  v.linv_exp = pl->linv_exp.as<int32_t>();
+  v.rows = rows;
+  if (pl->mixed) chk(mixed_maps_create(v, &pl->maps));
+  chk(cudaEventCreate(&pl->ev0));
+  chk(cudaEventCreate(&pl->ev1));
+  if (e != cudaSuccess) {
+    delete pl;
+    return BEOR_ECUDA;
+  }
+  *out = pl;
+  return BEOR_OK;
+}
+
+Plan* find_plan(beor_ctx* const* ctxs, int nsets, const int* Bs) {
+  for (Plan* p : g_plans) {
+    if ((int)p->ctxs.size() != nsets) continue;
+    bool same = true;
+    for (int s = 0; s < nsets && same; ++s) same = p->ctxs[s] == ctxs[s] && p->Bs[s] == Bs[s];
+    if (same) return p;
+  }
+  return nullptr;
+}
+
+void drop_plans_of(beor_ctx* c) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  std::vector<Plan*> keep;
+  for (Plan* p : g_plans) {
+    if (std::find(p->ctxs.begin(), p->ctxs.end(), c) != p->ctxs.end())
+      delete p;
+    else
+      keep.push_back(p);
+  }
+  g_plans.swap(keep);
+}
+
+int check_ready(const beor_ctx* c) {
+  if (!c) return BEOR_EINVAL;
+  if (c->poisoned) return BEOR_ESTATE;
+  return BEOR_OK;
+}
+
+int validate_kbin(const int32_t* kbin_host, int64_t n, int n_k) {
+  std::vector<int64_t> cnt(n_k, 0);
+  for (int64_t j = 0; j < n; ++j) {
+    int b = kbin_host[j];
+    if (b < -1 || b >= n_k) return BEOR_EINVAL;
+    if (b >= 0) cnt[b]++;
+  }
+  for (int i = 0; i < n_k; ++i)
+    if (cnt[i] == 0) return BEOR_EINVAL;
+  return BEOR_OK;
+}
+
+int set_kbin(beor_ctx* c, const int32_t* kbin, int64_t n, int n_k, double lssm) {
+  if (!kbin || n_k < 1 || !(lssm > 0.0) || !std::isfinite(lssm)) return BEOR_EINVAL;
+  std::vector<int32_t> h(n);
+  if (is_device_ptr(kbin)) {
+    CKC(c, cudaMemcpy(h.data(), kbin, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(h.data(), kbin, sizeof(int32_t) * n);
+  }
+  int r = validate_kbin(h.data(), n, n_k);
+  if (r) return r;
+  CKC(c, c->kbin.alloc(sizeof(int32_t) * n));
+  CKC(c, cudaMemcpy(c->kbin.p, h.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  c->n_k = n_k;
+  c->lssm_prior_var = lssm;
+  return BEOR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* beor_strerror(int code) {
+  switch (code) {
+    case BEOR_OK: return "ok";
+    case BEOR_EINVAL: return "invalid argument";
+    case BEOR_ENOMEM: return "out of memory";
+    case BEOR_ECUDA: return "CUDA error";
+    case BEOR_ETIMEOUT: return "device-side wait timed out";
+    case BEOR_ESTATE: return "call out of order or context poisoned";
+    case BEOR_ENOTSUP: return "not supported on this device";
+    default: return "unknown error";
+  }
+}
+
+int beor_create(beor_ctx** out, int device, int precision) {
+  if (!out || (precision != BEOR_PREC_FP64 && precision != BEOR_PREC_MIXED)) return BEOR_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return BEOR_EINVAL;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return BEOR_ECUDA;
+  if (precision == BEOR_PREC_MIXED && !mixed_supported(device)) return BEOR_ENOTSUP;
+  beor_ctx* c = new beor_ctx();
+  c->device = device;
+  c->precision = precision;
+  *out = c;
+  return BEOR_OK;
+}
+
+int beor_destroy(beor_ctx* c) {
+  if (!c) return BEOR_EINVAL;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  drop_plans_of(c);
+  delete c;
+  return BEOR_OK;
+}
+
+int beor_set_T(beor_ctx* c, const beor_c128* T, int64_t n_vis, int64_t n_model, int64_t ld,
+               const int32_t* kbin, int n_k, double lssm_prior_var) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (!T || n_vis <= 0 || n_model <= 0 || ld < n_model || n_model > (1 << 20)) return BEOR_EINVAL;
+  cudaSetDevice(c->device);
+  drop_plans_of(c);
+  r = set_kbin(c, kbin, n_model, n_k, lssm_prior_var);
+  if (r) return r;
+  c->model_kind = 1;
+  c->n_vis = n_vis;
+  c->n = (int)n_model;
+  c->nt = (int)((n_model + BEOR_TB - 1) / BEOR_TB);
+  c->ld = n_model;
+  c->A.release();
+  c->W.release();
+  CKC(c, c->T.alloc(sizeof(double2) * (size_t)n_vis * n_model));
+  if (ld == n_model) {
+    CKC(c, to_device(c->T.p, T, sizeof(double2) * (size_t)n_vis * n_model, 0));
+  } else {
+    CKC(c, cudaMemcpy2D(c->T.p, sizeof(double2) * n_model, T, sizeof(double2) * ld, sizeof(double2) * n_model,
+                        n_vis, is_device_ptr(T) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  }
+  CKC(c, cudaDeviceSynchronize());
+  c->have_data = false;
+  c->have_pre = false;
+  return BEOR_OK;
+}
+
+int beor_set_instrument(beor_ctx* c, const beor_c128* A, const beor_c128* W, int nf, int64_t ntb, int ncells,
+                        int nx, const int32_t* kbin, int n_k, double lssm_prior_var) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (!A || !W || nf <= 0 || ntb <= 0 || ncells <= 0 || nx <= 0) return BEOR_EINVAL;
+  int64_t n = (int64_t)ncells * nx;
+  if (n > (1 << 20)) return BEOR_EINVAL;
+  cudaSetDevice(c->device);
+  drop_plans_of(c);
+  r = set_kbin(c, kbin, n, n_k, lssm_prior_var);
+  if (r) return r;
+  c->model_kind = 2;
+  c->nf = nf;
+  c->ntb = ntb;
+  c->ncells = ncells;
+  c->nx = nx;
+  c->n_vis = (int64_t)nf * ntb;
+  c->n = (int)n;
+  c->nt = (int)((n + BEOR_TB - 1) / BEOR_TB);
+  c->T.release();
+  CKC(c, c->A.alloc(sizeof(double2) * (size_t)nf * ntb * ncells));
+  CKC(c, c->W.alloc(sizeof(double2) * (size_t)nf * nx));
+  CKC(c, to_device(c->A.p, A, sizeof(double2) * (size_t)nf * ntb * ncells, 0));
+  CKC(c, to_device(c->W.p, W, sizeof(double2) * (size_t)nf * nx, 0));
+  CKC(c, cudaDeviceSynchronize());
+  c->have_data = false;
+  c->have_pre = false;
+  return BEOR_OK;
+}
+
+int beor_set_data(beor_ctx* c, const beor_c128* d, const double* noise_var) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (c->model_kind == 0) return BEOR_ESTATE;
+  if (!d || !noise_var) return BEOR_EINVAL;
+  cudaSetDevice(c->device);
+  std::vector<double> nv(c->n_vis);
+  if (is_device_ptr(noise_var)) {
+    CKC(c, cudaMemcpy(nv.data(), noise_var, sizeof(double) * c->n_vis, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(nv.data(), noise_var, sizeof(double) * c->n_vis);
+  }
+  for (double x : nv)
+    if (!(x > 0.0) || !std::isfinite(x)) return BEOR_EINVAL;
+  for (double& x : nv) x = 1.0 / x;
+  CKC(c, c->w.alloc(sizeof(double) * c->n_vis));
+  CKC(c, cudaMemcpy(c->w.p, nv.data(), sizeof(double) * c->n_vis, cudaMemcpyHostToDevice));
+  CKC(c, c->d.alloc(sizeof(double2) * c->n_vis));
+  CKC(c, to_device(c->d.p, d, sizeof(double2) * c->n_vis, 0));
+  CKC(c, cudaDeviceSynchronize());
+  c->have_data = true;
+  c->have_pre = false;
+  drop_plans_of(c);
+  return BEOR_OK;
+}
+
+int beor_precompute(beor_ctx* c, void* stream) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (!c->have_data) return BEOR_ESTATE;
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  drop_plans_of(c);
+  CKC(c, c->M.alloc(sizeof(double2) * (size_t)tri_count(c->nt) * BEOR_TILE_ELEMS));
+  CKC(c, c->dbar.alloc(sizeof(double2) * (size_t)c->nt * BEOR_TB));
+  if (c->model_kind == 1) {
+    CKC(c, precompute_dense(c->T.as<double2>(), c->n_vis, c->n, c->ld, c->w.as<double>(), c->d.as<double2>(), c->nt,
+                            c->M.as<double2>(), c->dbar.as<double2>(), s));
+  } else {
+    DevBuf G, u;
+    CKC(c, G.alloc(sizeof(double2) * (size_t)c->nf * c->ncells * c->ncells));
+    CKC(c, u.alloc(sizeof(double2) * (size_t)c->nf * c->ncells));
+    CKC(c, precompute_factored(c->A.as<double2>(), c->W.as<double2>(), c->nf, c->ntb, c->ncells, c->nx,
+                               c->w.as<double>(), c->d.as<double2>(), c->n, c->nt, G.as<double2>(), u.as<double2>(),
+                               c->M.as<double2>(), c->dbar.as<double2>(), s));
+    CKC(c, cudaStreamSynchronize(s));
+  }
+  CKC(c, cudaStreamSynchronize(s));
+  c->have_pre = true;
+  return BEOR_OK;
+}
+
+int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, const int* B,
+                   double* const* lnl_out, int32_t* const* status_out, void* stream) {
+  if (!ctxs || nsets <= 0 || !phi || !B) return BEOR_EINVAL;
+  for (int s = 0; s < nsets; ++s) {
+    int r = check_ready(ctxs[s]);
+    if (r) return r;
+    if (!ctxs[s]->have_pre) return BEOR_ESTATE;
+    if (ctxs[s]->device != ctxs[0]->device || ctxs[s]->precision != ctxs[0]->precision) return BEOR_EINVAL;
+    if (B[s] <= 0 || B[s] > 4096 || !phi[s]) return BEOR_EINVAL;
+  }
+  beor_ctx* c0 = ctxs[0];
+  cudaSetDevice(c0->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Plan* pl = find_plan(ctxs, nsets, B);
+  if (!pl) {
+    int r = build_plan(ctxs, nsets, B, &pl);
+    if (r) return r;
+    g_plans.push_back(pl);
+  }
+  for (int s = 0; s < nsets; ++s) {
+    // validate phi values (finite) on the host when possible
+    size_t bytes = sizeof(double) * (size_t)B[s] * ctxs[s]->n_k;
+    if (!is_device_ptr(phi[s])) {
+      for (size_t i = 0; i < (size_t)B[s] * ctxs[s]->n_k; ++i)
+        if (!std::isfinite(phi[s][i])) return BEOR_EINVAL;
+    }
+    CKC(c0, to_device(pl->phis.as<double>() + pl->phi_off[s], phi[s], bytes, st));
+  }
+  if (!pl->exec) {
+    // first use: run once directly (sets kernel attributes), then capture
+    int64_t nl = 0;
+    CKC(c0, run_sequence(*pl, st, &nl));
+    pl->launches = nl;
+    CKC(c0, cudaStreamSynchronize(st));
+    cudaStream_t cs;
+    CKC(c0, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = run_sequence(*pl, cs, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->exec, g, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return fail_cuda(c0, e);
+    }
+    pl->graph = g;
+  } else {
+    CKC(c0, cudaEventRecord(pl->ev0, st));
+    CKC(c0, cudaGraphLaunch(pl->exec, st));
+    CKC(c0, cudaEventRecord(pl->ev1, st));
+  }
+  for (int s = 0; s < nsets; ++s) {
+    int f = pl->first[s];
+    if (lnl_out && lnl_out[s]) CKC(c0, from_device(lnl_out[s], pl->view.lnl + f, sizeof(double) * B[s], st));
+    if (status_out && status_out[s])
+      CKC(c0, from_device(status_out[s], pl->view.status + f, sizeof(int32_t) * B[s], st));
+  }
+  CKC(c0, cudaStreamSynchronize(st));
+  CKC(c0, cudaGetLastError());
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, pl->ev0, pl->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    ms = -1.0f;
+  }
+  // diagnostics
+  std::vector<double> resid(pl->P);
+  CKC(c0, cudaMemcpy(resid.data(), pl->view.resid, sizeof(double) * pl->P, cudaMemcpyDeviceToHost));
+  for (int s = 0; s < nsets; ++s) {
+    beor_ctx* c = ctxs[s];
+    c->stats.ms_last = ms;
+    c->stats.kernel_launches = pl->launches;
+    c->stats.refine_iters_max = pl->mixed ? kRefineIters : 0;
+    double mx = 0.0;
+    for (int b = 0; b < B[s]; ++b) mx = std::max(mx, resid[pl->first[s] + b]);
+    c->stats.resid_rel_max = mx;
+    c->last_plan = pl;
+    c->last_first = pl->first[s];
+  }
+  return BEOR_OK;
+}
+
+int beor_lnl(beor_ctx* c, const double* phi, int B, double* lnl_out, int32_t* status_out, void* stream) {
+  return beor_lnl_multi(&c, 1, &phi, &B, &lnl_out, &status_out, stream);
+}
+
+int beor_posterior_mean(beor_ctx* c, const double* phi, beor_c128* abar_out, int32_t* status_out, void* stream) {
+  if (!abar_out) return BEOR_EINVAL;
+  int32_t st = 0;
+  double l = 0.0;
+  int B = 1;
+  double* lo = &l;
+  int32_t* so = &st;
+  int r = beor_lnl_multi(&c, 1, &phi, &B, &lo, &so, stream);
+  if (r) return r;
+  Plan* pl = c->last_plan;
+  CKC(c, from_device(abar_out, pl->view.vec_x + pl->h_prob[c->last_first].row_off, sizeof(double2) * c->n,
+                     (cudaStream_t)stream));
+  CKC(c, cudaStreamSynchronize((cudaStream_t)stream));
+  if (status_out) {
+    if (is_device_ptr(status_out))
+      CKC(c, cudaMemcpy(status_out, &st, sizeof(int32_t), cudaMemcpyHostToDevice));
+    else
+      *status_out = st;
+  }
+  return BEOR_OK;
+}
+
+int beor_get_model_dims(const beor_ctx* c, int64_t* n_vis, int64_t* n_model, int* n_k) {
+  if (!c) return BEOR_EINVAL;
+  if (n_vis) *n_vis = c->n_vis;
+  if (n_model) *n_model = c->n;
+  if (n_k) *n_k = c->n_k;
+  return BEOR_OK;
+}
+
+int beor_get_M(beor_ctx* c, beor_c128* M_out) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (!c->have_pre || !M_out) return c->have_pre ? BEOR_EINVAL : BEOR_ESTATE;
+  cudaSetDevice(c->device);
+  std::vector<double2> t((size_t)tri_count(c->nt) * BEOR_TILE_ELEMS);
+  CKC(c, cudaMemcpy(t.data(), c->M.p, sizeof(double2) * t.size(), cudaMemcpyDeviceToHost));
+  const int64_t n = c->n;
+  std::vector<double2> full((size_t)n * n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j <= i; ++j) {
+      int I = (int)(i / BEOR_TB), J = (int)(j / BEOR_TB);
+      double2 v = t[(size_t)(tri_index(I, J) * BEOR_TILE_ELEMS + (j % BEOR_TB) * BEOR_TB + (i % BEOR_TB))];
+      full[(size_t)(i * n + j)] = v;
+      full[(size_t)(j * n + i)] = make_double2(v.x, -v.y);
+    }
+  if (is_device_ptr(M_out)) {
+    CKC(c, cudaMemcpy(M_out, full.data(), sizeof(double2) * full.size(), cudaMemcpyHostToDevice));
+  } else {
+    std::memcpy(M_out, full.data(), sizeof(double2) * full.size());
+  }
+  return BEOR_OK;
+}
+
+int beor_get_dbar(beor_ctx* c, beor_c128* out) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (!c->have_pre) return BEOR_ESTATE;
+  if (!out) return BEOR_EINVAL;
+  cudaSetDevice(c->device);
+  CKC(c, from_device(out, c->dbar.p, sizeof(double2) * c->n, 0));
+  CKC(c, cudaDeviceSynchronize());
+  return BEOR_OK;
+}
+
+int beor_get_stats(const beor_ctx* c, beor_stats* out) {
+  if (!c || !out) return BEOR_EINVAL;
+  *out = c->stats;
+  return BEOR_OK;
+}
+
+int beor_get_terms(const beor_ctx* c, double* logdet_phi, double* logdet_sigma, double* q, int B) {
+  if (!c || !c->last_plan) return BEOR_ESTATE;
+  Plan* pl = c->last_plan;
+  int f = c->last_first;
+  if (B <= 0 || f + B > pl->P) return BEOR_EINVAL;
+  cudaSetDevice(c->device);
+  if (logdet_phi) CKC(nullptr, cudaMemcpy(logdet_phi, pl->view.logdet_phi + f, sizeof(double) * B, cudaMemcpyDeviceToHost));
+  if (logdet_sigma)
+    CKC(nullptr, cudaMemcpy(logdet_sigma, pl->view.logdet_sigma + f, sizeof(double) * B, cudaMemcpyDeviceToHost));
+  if (q) CKC(nullptr, cudaMemcpy(q, pl->view.q + f, sizeof(double) * B, cudaMemcpyDeviceToHost));
+  return BEOR_OK;
+}
+
+}  // extern "C"

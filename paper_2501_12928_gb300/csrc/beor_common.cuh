@@ -1,0 +1,95 @@
+// Shared definitions of the GB300 likelihood library (device and host side).
+//
+// Matrix storage used by every factorisation kernel ("packed tiles"):
+//   an N x N Hermitian matrix is padded to Np = nt*128 and stored as its
+//   lower-triangular 128 x 128 tiles (i >= j), tile (i, j) at tile index
+//   i*(i+1)/2 + j, each tile column-major (element (r, c) at c*128 + r) so
+//   that 32 lanes handling 32 consecutive rows touch 32 consecutive elements.
+// Element types: double2 {re, im} (float64 path) or float4
+//   {re_hi, re_lo, im_hi, im_lo} (double-float pair per real number; the
+//   mixed path's working matrix).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#define BEOR_TB 128                       // tile edge (complex rows / cols)
+#define BEOR_TILE_ELEMS (BEOR_TB * BEOR_TB)
+#define BEOR_NSLICE 5                     // bf16 slices per real value (mixed path)
+#define BEOR_NPLANE (2 * BEOR_NSLICE)     // (slice, re/im) planes
+
+namespace beor {
+
+__host__ __device__ inline int64_t tri_index(int i, int j) { return (int64_t)i * (i + 1) / 2 + j; }
+__host__ __device__ inline int64_t tri_count(int nt) { return (int64_t)nt * (nt + 1) / 2; }
+
+// One matrix to factorise: prior point b of instrument set s.
+struct Prob {
+  int n;              // model dimension
+  int nt;             // tiles per side
+  int set;            // instrument set index
+  int b;              // index within the set's batch
+  int64_t ws_off;     // element offset of tile (0,0) in the workspace
+  int64_t dinv_off;   // element offset (double2) of this problem's inverse diagonal blocks
+  int64_t row_off;    // row offset of this problem in the panel-slice and vector buffers
+};
+
+// One instrument (shared by all prior points of the set).
+struct SetDesc {
+  int n, nt, n_k;
+  double lssm_prior_var;
+  const double2* M;       // packed tiles (float64), lower
+  const double2* dbar;    // Np
+  const int32_t* kbin;    // n
+  const double* phi;      // B x n_k (device staging)
+};
+
+// Bounds of the per-call device state shared by kernels.
+struct Flags {
+  int error;              // nonzero: a device-side bounded wait gave up (code)
+  int pad[31];
+};
+
+// ---------------------------------------------------------------------------
+// double-float helpers (Dekker / Knuth error-free transformations, FMA based)
+// ---------------------------------------------------------------------------
+struct dfl { float hi, lo; };
+
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ dfl df_fast_two_sum(float a, float b) {
+  float s = a + b;
+  float e = b - (s - a);
+  return {s, e};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  dfl s = df_two_sum(a.hi, b.hi);
+  dfl t = df_two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = df_fast_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return df_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+// a + b*c (b, c double-float)
+__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return df_add(a, df_mul(b, c)); }
+__device__ __forceinline__ dfl df_from_double(double x) {
+  float h = (float)x;
+  float l = (float)(x - (double)h);
+  return {h, l};
+}
+__device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace beor

@@ -1,0 +1,71 @@
+// Host-side launchers shared between the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "beor_common.cuh"
+
+namespace beor {
+
+// precompute.cu
+cudaError_t precompute_dense(const double2* T, int64_t n_vis, int n, int64_t ld, const double* w,
+                             const double2* d, int nt, double2* Mt, double2* dbar, cudaStream_t s);
+cudaError_t precompute_factored(const double2* A, const double2* W, int nf, int64_t ntb, int ncells,
+                                int nx, const double* w, const double2* d, int n, int nt,
+                                double2* G_scratch, double2* u_scratch, double2* Mt, double2* dbar,
+                                cudaStream_t s);
+
+// Device-side view of one batched evaluation (all problems of all sets).
+struct BatchView {
+  int P;                     // problems
+  int nsets;
+  const Prob* prob;          // [P]
+  const SetDesc* sets;       // [nsets]
+  int max_nt;
+  // workspaces
+  void* ws;                  // packed tiles of every problem (double2 or float4)
+  double2* dinv;             // inverse diagonal blocks, packed lower 128x128 per block
+  double* phi_inv;           // [rows] prior inverse per problem row (padded rows = 1)
+  double2* vec_b;            // [rows] right-hand side / residual
+  double2* vec_y;            // [rows] forward-solve result
+  double2* vec_x;            // [rows] solution
+  double2* vec_t;            // [rows] solve scratch
+  double2* vec_r;            // [rows] refinement residual
+  double2* vec_d;            // [rows] refinement correction
+  double* logdet_phi;        // [P]
+  double* logdet_sigma;      // [P]
+  double* q;                 // [P]
+  double* lnl;               // [P]
+  int32_t* status;           // [P]
+  double* resid;             // [P] refinement residual norm ratio
+  Flags* flags;
+  // mixed path slice buffers
+  __nv_bfloat16* panel_sl;   // [NPLANE][rows][128]
+  int32_t* panel_exp;        // [rows]
+  __nv_bfloat16* linv_sl;    // [NPLANE][P*128][128]
+  int32_t* linv_exp;         // [P*128]
+  int64_t rows;              // sum of padded dimensions
+};
+
+// chol.cu (both precisions)
+cudaError_t launch_prior_init(const BatchView& v, bool mixed, cudaStream_t s);
+cudaError_t launch_diag(const BatchView& v, int k, bool mixed, cudaStream_t s);
+cudaError_t launch_panel_f64(const BatchView& v, int k, cudaStream_t s);
+cudaError_t launch_trail_f64(const BatchView& v, int k, cudaStream_t s);
+cudaError_t launch_solve(const BatchView& v, bool mixed, const double2* rhs, double2* out, cudaStream_t s);
+cudaError_t launch_lnl(const BatchView& v, cudaStream_t s);
+cudaError_t launch_copy_dbar(const BatchView& v, cudaStream_t s);
+
+// mixed.cu
+struct MixedMaps;  // opaque TMA descriptors of one batch
+cudaError_t mixed_maps_create(const BatchView& v, MixedMaps** out);
+void mixed_maps_destroy(MixedMaps* m);
+cudaError_t launch_slice_panel(const BatchView& v, int k, cudaStream_t s);
+cudaError_t launch_panel_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s);
+cudaError_t launch_trail_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s);
+cudaError_t launch_residual(const BatchView& v, cudaStream_t s);      // vec_r = dbar - Sigma x (float64)
+cudaError_t launch_refine_update(const BatchView& v, cudaStream_t s); // x += vec_d; residual norm
+int mixed_supported(int device);
+
+}  // namespace beor

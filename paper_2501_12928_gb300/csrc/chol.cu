@@ -1,0 +1,568 @@
+// Blocked right-looking complex Cholesky of Sigma = M + Phi^-1 for a batch of
+// problems, the triangular solves for abar = Sigma^-1 dbar, and the lnL
+// assembly (lnL = -1/2 log|Phi| - 1/2 log|Sigma| + 1/2 dbar^H abar).
+//
+// Kernels here serve both precisions:
+//  * prior / init:  Phi^-1 from phi (one amplitude per k bin, Eq. for P(k_i)),
+//                   log|Phi|, and the working matrix W = M + diag(Phi^-1);
+//  * diag:          float64 factorisation and inversion of the 128 x 128
+//                   diagonal block, log|Sigma| accumulation, status;
+//  * panel/trail:   float64 tile GEMMs (the float64 comparator path);
+//  * solve:         blocked forward / backward substitution;
+//  * lnl:           q = Re(dbar^H abar) and lnL.
+#include <cmath>
+
+#include "beor_common.cuh"
+#include "beor_internal.h"
+
+namespace beor {
+
+// --------------------------------------------------------------------------
+// workspace element access
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double2 ws_load(const double2* p) { return *p; }
+__device__ __forceinline__ double2 ws_load(const float4* p) {
+  float4 v = *p;
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+__device__ __forceinline__ void ws_store(double2* p, double2 v) { *p = v; }
+__device__ __forceinline__ void ws_store(float4* p, double2 v) {
+  float rh = (float)v.x, ih = (float)v.y;
+  *p = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
+__device__ __forceinline__ void tile_of(int64_t t, int& I, int& J) {
+  int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while ((int64_t)i * (i + 1) / 2 > t) --i;
+  while ((int64_t)(i + 1) * (i + 2) / 2 <= t) ++i;
+  I = i;
+  J = (int)(t - (int64_t)i * (i + 1) / 2);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// --------------------------------------------------------------------------
+// prior: Phi^-1 per row, log|Phi| per problem, reset of the per-problem sums
+// --------------------------------------------------------------------------
+__global__ void prior_kernel(BatchView v) {
+  const int p = blockIdx.x;
+  const Prob pr = v.prob[p];
+  const SetDesc sd = v.sets[pr.set];
+  const double* phi = sd.phi + (int64_t)pr.b * sd.n_k;
+  const double ln10 = 2.302585092994045684;
+  __shared__ double red[33];
+  double acc = 0.0;
+  const int np = pr.nt * BEOR_TB;
+  for (int j = threadIdx.x; j < np; j += blockDim.x) {
+    double inv = 1.0;
+    if (j < pr.n) {
+      int kb = sd.kbin[j];
+      if (kb >= 0) {
+        double ph = phi[kb];
+        inv = exp10(-ph);
+        acc += ph * ln10;
+      } else {
+        inv = 1.0 / sd.lssm_prior_var;
+        acc += log(sd.lssm_prior_var);
+      }
+    }
+    v.phi_inv[pr.row_off + j] = inv;
+  }
+  double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    v.logdet_phi[p] = tot;
+    v.logdet_sigma[p] = 0.0;
+    v.status[p] = 0;
+    v.resid[p] = 0.0;
+  }
+}
+
+template <typename WS>
+__global__ void init_ws_kernel(BatchView v) {
+  const int p = blockIdx.y;
+  const Prob pr = v.prob[p];
+  const SetDesc sd = v.sets[pr.set];
+  WS* ws = reinterpret_cast<WS*>(v.ws) + pr.ws_off;
+  const int64_t total = tri_count(pr.nt) * BEOR_TILE_ELEMS;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    double2 m = sd.M[e];
+    int64_t t = e / BEOR_TILE_ELEMS;
+    int w = (int)(e % BEOR_TILE_ELEMS);
+    int r = w % BEOR_TB, c = w / BEOR_TB;
+    int I, J;
+    tile_of(t, I, J);
+    if (I == J && r == c) {
+      m.x += v.phi_inv[pr.row_off + I * BEOR_TB + r];
+      m.y = 0.0;
+    }
+    ws_store(ws + e, m);
+  }
+}
+
+cudaError_t launch_prior_init(const BatchView& v, bool mixed, cudaStream_t s) {
+  prior_kernel<<<v.P, 256, 0, s>>>(v);
+  dim3 g(512, v.P);
+  if (mixed)
+    init_ws_kernel<float4><<<g, 256, 0, s>>>(v);
+  else
+    init_ws_kernel<double2><<<g, 256, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// bf16 slicing of one row of 128 complex values (mixed path operands).
+// value = 2^(e-7) * sum_s slice_s, slice_s = sigma_s * 2^(-8 s), sigma_s an
+// integer with |sigma_s| <= 128; exact in float64 arithmetic.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int row_exponent(double mx) {
+  if (!(mx > 0.0)) return -1000;
+  return ilogb(mx) + 1;
+}
+__device__ __forceinline__ void slice_value(double x, int e, __nv_bfloat16* out, int64_t plane_stride) {
+  if (e <= -1000) {
+#pragma unroll
+    for (int s = 0; s < BEOR_NSLICE; ++s) out[s * plane_stride] = __float2bfloat16_rn(0.0f);
+    return;
+  }
+  double y = ldexp(x, 7 - e);
+#pragma unroll
+  for (int s = 0; s < BEOR_NSLICE; ++s) {
+    double q = rint(y);
+    y = (y - q) * 256.0;
+    out[s * plane_stride] = __float2bfloat16_rn((float)ldexp(q, -8 * s));
+  }
+}
+
+// --------------------------------------------------------------------------
+// diagonal block: float64 Cholesky + inverse, log-det, status
+// --------------------------------------------------------------------------
+#define DG_PACK (BEOR_TB * (BEOR_TB + 1) / 2)
+__device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
+
+template <typename WS>
+__global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed) {
+  extern __shared__ double2 dsm[];
+  double2* A = dsm;                    // packed lower 128x128
+  double2* col = dsm + DG_PACK;        // 128
+  __shared__ int s_fail;
+  const int p = blockIdx.x;
+  const Prob pr = v.prob[p];
+  if (k >= pr.nt) return;
+  if (v.status[p] != 0) return;
+  WS* ws = reinterpret_cast<WS*>(v.ws) + pr.ws_off + tri_index(k, k) * BEOR_TILE_ELEMS;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int e = tid; e < BEOR_TILE_ELEMS; e += nthr) {
+    int r = e % BEOR_TB, c = e / BEOR_TB;
+    if (r >= c) A[pk(r, c)] = ws_load(ws + e);
+  }
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  double ld = 0.0;   // thread 0 accumulates
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
+  for (int j = 0; j < BEOR_TB; ++j) {
+    if (tid == 0) {
+      double d = A[pk(j, j)].x;
+      if (!(d > 0.0) || !isfinite(d)) {
+        s_fail = k * BEOR_TB + j + 1;
+      } else {
+        double l = sqrt(d);
+        A[pk(j, j)] = make_double2(l, 0.0);
+        if (k * BEOR_TB + j < pr.n) ld += 2.0 * log(l);
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    const double inv = 1.0 / A[pk(j, j)].x;
+    for (int i = j + 1 + tid; i < BEOR_TB; i += nthr) {
+      double2 a = A[pk(i, j)];
+      a.x *= inv;
+      a.y *= inv;
+      A[pk(i, j)] = a;
+      col[i] = a;
+    }
+    __syncthreads();
+    for (int i = j + 1 + warp; i < BEOR_TB; i += nwarp) {
+      double2 ai = col[i];
+      for (int l = j + 1 + lane; l <= i; l += 32) {
+        double2 al = col[l];
+        double2 x = A[pk(i, l)];
+        // x -= ai * conj(al)
+        x.x -= ai.x * al.x + ai.y * al.y;
+        x.y -= ai.y * al.x - ai.x * al.y;
+        A[pk(i, l)] = x;
+      }
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (tid == 0) v.status[p] = s_fail;
+    return;
+  }
+  if (tid == 0) v.logdet_sigma[p] += ld;
+  // L_kk back to the workspace tile (upper part zero)
+  for (int e = tid; e < BEOR_TILE_ELEMS; e += nthr) {
+    int r = e % BEOR_TB, c = e / BEOR_TB;
+    ws_store(ws + e, r >= c ? A[pk(r, c)] : make_double2(0.0, 0.0));
+  }
+  __syncthreads();
+  // in-place inverse, row by row: Linv[i][j] = -(sum_{m=j}^{i-1} L[i][m] Linv[m][j]) / L[i][i]
+  for (int i = 0; i < BEOR_TB; ++i) {
+    const double lii = A[pk(i, i)].x;
+    double2 t = make_double2(0.0, 0.0);
+    if (tid < i) {
+      const int j = tid;
+      double sr = 0.0, si = 0.0;
+      for (int m = j; m < i; ++m) {
+        double2 a = A[pk(i, m)], b = A[pk(m, j)];
+        sr = fma(a.x, b.x, fma(-a.y, b.y, sr));
+        si = fma(a.x, b.y, fma(a.y, b.x, si));
+      }
+      t = make_double2(-sr / lii, -si / lii);
+    }
+    __syncthreads();
+    if (tid < i) A[pk(i, tid)] = t;
+    if (tid == i) A[pk(i, i)] = make_double2(1.0 / lii, 0.0);
+    __syncthreads();
+  }
+  double2* dinv = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
+  for (int e = tid; e < DG_PACK; e += nthr) dinv[e] = A[e];
+  if (mixed) {
+    // slices of Linv rows (B operand of the panel product L_ik = A_ik Linv^H)
+    if (tid < BEOR_TB) {
+      const int c = tid;
+      double mx = 0.0;
+      for (int m = 0; m <= c; ++m) {
+        double2 a = A[pk(c, m)];
+        mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
+      }
+      int e = row_exponent(mx);
+      const int64_t row = (int64_t)p * BEOR_TB + c;
+      const int64_t lrows = (int64_t)v.P * BEOR_TB;
+      v.linv_exp[row] = e;
+      const int64_t ps = 2 * lrows * BEOR_TB;   // stride between slices (two planes each)
+      for (int m = 0; m < BEOR_TB; ++m) {
+        double2 a = m <= c ? A[pk(c, m)] : make_double2(0.0, 0.0);
+        slice_value(a.x, e, v.linv_sl + (0 * lrows + row) * BEOR_TB + m, ps);
+        slice_value(a.y, e, v.linv_sl + (1 * lrows + row) * BEOR_TB + m, ps);
+      }
+    }
+  }
+}
+
+cudaError_t launch_diag(const BatchView& v, int k, bool mixed, cudaStream_t s) {
+  const size_t smem = sizeof(double2) * (DG_PACK + BEOR_TB);
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(diag_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(diag_kernel<float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    init = true;
+  }
+  if (mixed)
+    diag_kernel<float4><<<v.P, 512, smem, s>>>(v, k, 1);
+  else
+    diag_kernel<double2><<<v.P, 512, smem, s>>>(v, k, 0);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// float64 panel: L_ik = A_ik Linv_kk^H for i > k (rows split in two halves)
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) panel_f64_kernel(BatchView v, int k) {
+  extern __shared__ double2 psm[];
+  double2* xs = psm;                  // [128 m][64 r]
+  double2* ys = psm + 128 * 64;       // [16 m][128 c]
+  const int p = blockIdx.y;
+  const Prob pr = v.prob[p];
+  const int i = k + 1 + (blockIdx.x >> 1);
+  if (i >= pr.nt || v.status[p] != 0) return;
+  const int r0 = (blockIdx.x & 1) * 64;
+  double2* tile = reinterpret_cast<double2*>(v.ws) + pr.ws_off + tri_index(i, k) * BEOR_TILE_ELEMS;
+  const double2* linv = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
+  for (int e = threadIdx.x; e < 128 * 64; e += 256) {
+    int m = e / 64, r = e % 64;
+    xs[e] = tile[m * BEOR_TB + r0 + r];
+  }
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double ar[4][8], ai[4][8];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) ar[a][b] = ai[a][b] = 0.0;
+  for (int m0 = 0; m0 < BEOR_TB; m0 += 16) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 16 * 128; e += 256) {
+      int mm = e / 128, c = e % 128, m = m0 + mm;
+      ys[e] = m <= c ? linv[pk(c, m)] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int mm = 0; mm < 16; ++mm) {
+      double2 x[4], y[8];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) x[a] = xs[(m0 + mm) * 64 + ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) y[b] = ys[mm * 128 + tx * 8 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          // x * conj(y)
+          ar[a][b] = fma(x[a].x, y[b].x, fma(x[a].y, y[b].y, ar[a][b]));
+          ai[a][b] = fma(x[a].y, y[b].x, fma(-x[a].x, y[b].y, ai[a][b]));
+        }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      int r = r0 + ty * 4 + a, c = tx * 8 + b;
+      tile[c * BEOR_TB + r] = make_double2(ar[a][b], ai[a][b]);
+    }
+}
+
+cudaError_t launch_panel_f64(const BatchView& v, int k, cudaStream_t s) {
+  int nblk = 2 * (v.max_nt - 1 - k);
+  if (nblk <= 0) return cudaSuccess;
+  const size_t smem = sizeof(double2) * (128 * 64 + 16 * 128);
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(panel_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    init = true;
+  }
+  panel_f64_kernel<<<dim3(nblk, v.P), 256, smem, s>>>(v, k);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// float64 trailing update: A_ij -= L_ik L_jk^H, k < j <= i, 64 x 64 sub-tiles
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) trail_f64_kernel(BatchView v, int k) {
+  __shared__ double2 xs[16][64];
+  __shared__ double2 ys[16][64];
+  const int p = blockIdx.y;
+  const Prob pr = v.prob[p];
+  const int T = pr.nt - k - 1;
+  const int64_t t = blockIdx.x >> 2;
+  if (T <= 0 || t >= tri_count(T) || v.status[p] != 0) return;
+  const int si = (blockIdx.x >> 1) & 1, sj = blockIdx.x & 1;
+  int a, b;
+  tile_of(t, a, b);
+  const int i = k + 1 + a, j = k + 1 + b;
+  if (i == j && si < sj) return;   // upper part of a diagonal tile is never read
+  double2* ws = reinterpret_cast<double2*>(v.ws) + pr.ws_off;
+  const double2* X = ws + tri_index(i, k) * BEOR_TILE_ELEMS + si * 64;
+  const double2* Y = ws + tri_index(j, k) * BEOR_TILE_ELEMS + sj * 64;
+  double2* C = ws + tri_index(i, j) * BEOR_TILE_ELEMS;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double ar[4][4], ai[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) ar[q][w] = ai[q][w] = 0.0;
+  for (int m0 = 0; m0 < BEOR_TB; m0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      int mm = e / 64, r = e % 64;
+      xs[mm][r] = X[(m0 + mm) * BEOR_TB + r];
+      ys[mm][r] = Y[(m0 + mm) * BEOR_TB + r];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int mm = 0; mm < 16; ++mm) {
+      double2 x[4], y[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        x[q] = xs[mm][ty * 4 + q];
+        y[q] = ys[mm][tx * 4 + q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          ar[q][w] = fma(x[q].x, y[w].x, fma(x[q].y, y[w].y, ar[q][w]));
+          ai[q][w] = fma(x[q].y, y[w].x, fma(-x[q].x, y[w].y, ai[q][w]));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      int r = si * 64 + ty * 4 + q, c = sj * 64 + tx * 4 + w;
+      double2 cv = C[c * BEOR_TB + r];
+      cv.x -= ar[q][w];
+      cv.y -= ai[q][w];
+      C[c * BEOR_TB + r] = cv;
+    }
+}
+
+cudaError_t launch_trail_f64(const BatchView& v, int k, cudaStream_t s) {
+  int T = v.max_nt - k - 1;
+  if (T <= 0) return cudaSuccess;
+  int64_t nblk = tri_count(T) * 4;
+  trail_f64_kernel<<<dim3((unsigned)nblk, v.P), 256, 0, s>>>(v, k);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Triangular solves with the factor: out = L^-H L^-1 rhs.  One CTA per
+// problem; diagonal blocks through the float64 inverse, off-diagonal tiles
+// in float64 (both element types are read as float64).
+// --------------------------------------------------------------------------
+template <typename WS>
+__global__ void __launch_bounds__(256) solve_kernel(BatchView v, const double2* __restrict__ rhs,
+                                                    double2* __restrict__ out) {
+  __shared__ double2 rk[BEOR_TB];
+  __shared__ double2 yk[BEOR_TB];
+  const int p = blockIdx.x;
+  const Prob pr = v.prob[p];
+  if (v.status[p] > 0) return;
+  const int np = pr.nt * BEOR_TB;
+  const WS* ws = reinterpret_cast<const WS*>(v.ws) + pr.ws_off;
+  double2* r = v.vec_t + pr.row_off;
+  double2* y = v.vec_y + pr.row_off;
+  double2* x = out + pr.row_off;
+  const double2* b = rhs + pr.row_off;
+  const int tid = threadIdx.x;
+  for (int j = tid; j < np; j += blockDim.x) r[j] = b[j];
+  __syncthreads();
+  // forward: L y = b
+  for (int k = 0; k < pr.nt; ++k) {
+    if (tid < BEOR_TB) rk[tid] = r[k * BEOR_TB + tid];
+    __syncthreads();
+    const double2* li = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
+    if (tid < BEOR_TB) {
+      double sr = 0.0, si = 0.0;
+      for (int m = 0; m <= tid; ++m) {
+        double2 a = li[pk(tid, m)], q = rk[m];
+        sr = fma(a.x, q.x, fma(-a.y, q.y, sr));
+        si = fma(a.x, q.y, fma(a.y, q.x, si));
+      }
+      yk[tid] = make_double2(sr, si);
+      y[k * BEOR_TB + tid] = yk[tid];
+    }
+    __syncthreads();
+    for (int i = k + 1 + (tid >> 7); i < pr.nt; i += 2) {
+      const int row = tid & 127;
+      const WS* t = ws + tri_index(i, k) * BEOR_TILE_ELEMS;
+      double sr = 0.0, si = 0.0;
+      for (int m = 0; m < BEOR_TB; ++m) {
+        double2 a = ws_load(t + m * BEOR_TB + row), q = yk[m];
+        sr = fma(a.x, q.x, fma(-a.y, q.y, sr));
+        si = fma(a.x, q.y, fma(a.y, q.x, si));
+      }
+      double2 cur = r[i * BEOR_TB + row];
+      r[i * BEOR_TB + row] = make_double2(cur.x - sr, cur.y - si);
+    }
+    __syncthreads();
+  }
+  // backward: L^H x = y
+  for (int j = tid; j < np; j += blockDim.x) r[j] = y[j];
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int k = pr.nt - 1; k >= 0; --k) {
+    if (tid < BEOR_TB) rk[tid] = r[k * BEOR_TB + tid];
+    __syncthreads();
+    const double2* li = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
+    if (tid < BEOR_TB) {
+      double sr = 0.0, si = 0.0;
+      for (int m = tid; m < BEOR_TB; ++m) {
+        double2 a = li[pk(m, tid)], q = rk[m];
+        // conj(a) * q
+        sr = fma(a.x, q.x, fma(a.y, q.y, sr));
+        si = fma(a.x, q.y, fma(-a.y, q.x, si));
+      }
+      yk[tid] = make_double2(sr, si);
+      x[k * BEOR_TB + tid] = yk[tid];
+    }
+    __syncthreads();
+    // r_i -= L_ki^H x_k for i < k: one warp per column c' of tile (k, i)
+    for (int i = 0; i < k; ++i) {
+      const WS* t = ws + tri_index(k, i) * BEOR_TILE_ELEMS;
+      for (int c = warp; c < BEOR_TB; c += (int)(blockDim.x >> 5)) {
+        double sr = 0.0, si = 0.0;
+        for (int m = lane; m < BEOR_TB; m += 32) {
+          double2 a = ws_load(t + c * BEOR_TB + m), q = yk[m];
+          sr = fma(a.x, q.x, fma(a.y, q.y, sr));
+          si = fma(a.x, q.y, fma(-a.y, q.x, si));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) {
+          double2 cur = r[i * BEOR_TB + c];
+          r[i * BEOR_TB + c] = make_double2(cur.x - sr, cur.y - si);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_solve(const BatchView& v, bool mixed, const double2* rhs, double2* out, cudaStream_t s) {
+  if (mixed)
+    solve_kernel<float4><<<v.P, 256, 0, s>>>(v, rhs, out);
+  else
+    solve_kernel<double2><<<v.P, 256, 0, s>>>(v, rhs, out);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// dbar of each problem's set into the right-hand-side vector
+// --------------------------------------------------------------------------
+__global__ void copy_dbar_kernel(BatchView v) {
+  const int p = blockIdx.x;
+  const Prob pr = v.prob[p];
+  const SetDesc sd = v.sets[pr.set];
+  const int np = pr.nt * BEOR_TB;
+  for (int j = threadIdx.x; j < np; j += blockDim.x) v.vec_b[pr.row_off + j] = sd.dbar[j];
+}
+
+cudaError_t launch_copy_dbar(const BatchView& v, cudaStream_t s) {
+  copy_dbar_kernel<<<v.P, 256, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// lnL = -1/2 log|Phi| - 1/2 log|Sigma| + 1/2 Re(dbar^H x)
+// --------------------------------------------------------------------------
+__global__ void lnl_kernel(BatchView v) {
+  const int p = blockIdx.x;
+  const Prob pr = v.prob[p];
+  const SetDesc sd = v.sets[pr.set];
+  __shared__ double red[33];
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < pr.n; j += blockDim.x) {
+    double2 d = sd.dbar[j], x = v.vec_x[pr.row_off + j];
+    acc += d.x * x.x + d.y * x.y;
+  }
+  double q = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    v.q[p] = q;
+    if (v.status[p] > 0)
+      v.lnl[p] = -INFINITY;
+    else
+      v.lnl[p] = -0.5 * v.logdet_phi[p] - 0.5 * v.logdet_sigma[p] + 0.5 * q;
+  }
+}
+
+cudaError_t launch_lnl(const BatchView& v, cudaStream_t s) {
+  lnl_kernel<<<v.P, 256, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+}  // namespace beor
