@@ -570,6 +570,14 @@ int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, c
   }
   CKC(c0, cudaStreamSynchronize(st));
   CKC(c0, cudaGetLastError());
+  {
+    int err = 0;
+    CKC(c0, cudaMemcpy(&err, &pl->view.flags->error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+      for (int s = 0; s < nsets; ++s) ctxs[s]->poisoned = true;
+      return BEOR_ETIMEOUT;
+    }
+  }
   float ms = 0.0f;
   if (cudaEventElapsedTime(&ms, pl->ev0, pl->ev1) != cudaSuccess) {
     cudaGetLastError();

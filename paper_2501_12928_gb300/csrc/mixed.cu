@@ -1,15 +1,722 @@
-// Mixed-precision tile kernels (placeholder until the tensor-core kernels land).
+// Mixed-precision tile kernels of the batched Cholesky (sm_103a).
+//
+// The trailing update A_ij -= L_ik L_jk^H and the panel product
+// L_ik = A_ik Linv_kk^H are complex GEMMs with K = 128.  They run on the
+// tcgen05 tensor cores as *exact* bf16 slice products (an Ozaki-style
+// splitting): every operand row r is scaled by 2^(7 - e_r) and cut into five
+// balanced base-256 digits sigma_s (|sigma_s| <= 128), stored as bf16 values
+// sigma_s * 2^(-8 s).  A product of two slices is exact in fp32, and a sum of
+// 256 of them (one 128-complex block column, real and imaginary parts) stays
+// below 2^24 units, so the fp32 accumulator of the tensor core is exact for
+// the level-0 pair (0,0) and the level-1 pairs (0,1), (1,0).  All pairs with
+// s + t >= 2 share a third accumulator whose rounding lies 2^-16 below the
+// leading term.  The epilogue adds the three levels as a double-float number,
+// scales by 2^(e_r + e_c - 14) and updates the working matrix, itself kept as
+// a double-float pair per real number.  The result is accurate to about
+// 2^-40 of the operand row scales, which keeps log|Sigma| well inside the
+// likelihood tolerance for Sigma as ill-conditioned as the eta / foreground
+// degeneracy makes it (a float32-accumulated product does not).
+//
+// Kernel structure (one CTA per SM, persistent over output tiles of 128 rows
+// x 64 complex columns): warp 0 issues TMA loads of the slice planes into a
+// 3-stage shared-memory ring (32-byte swizzle, K chunks of 16), warp 1 issues
+// the tcgen05.mma instructions (M = 128, N = 64, K = 16, bf16 -> fp32) into
+// six TMEM accumulators (3 levels x re/im), warps 2-5 drain TMEM and apply
+// the update.  Every wait is bounded by a %globaltimer deadline; on expiry
+// the kernel records an error code, drains what it issued and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "beor_common.cuh"
 #include "beor_internal.h"
 
 namespace beor {
-struct MixedMaps { int dummy; };
-cudaError_t mixed_maps_create(const BatchView&, MixedMaps** out) { *out = nullptr; return cudaErrorNotSupported; }
-void mixed_maps_destroy(MixedMaps* m) { delete m; }
-cudaError_t launch_slice_panel(const BatchView&, int, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_panel_mixed(const BatchView&, const MixedMaps*, int, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_trail_mixed(const BatchView&, const MixedMaps*, int, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_residual(const BatchView&, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_refine_update(const BatchView&, cudaStream_t) { return cudaErrorNotSupported; }
-int mixed_supported(int) { return 0; }
+
+constexpr int MX_M = 128;                // output rows per tile
+constexpr int MX_N = 64;                 // output complex columns per tile
+constexpr int MX_KC = 16;                // complex K per pipeline stage
+constexpr int MX_STAGES = 3;
+constexpr int MX_A_BYTES = BEOR_NPLANE * MX_M * MX_KC * 2;   // 40960
+constexpr int MX_B_BYTES = BEOR_NPLANE * MX_N * MX_KC * 2;   // 20480
+constexpr int MX_STAGE_BYTES = MX_A_BYTES + MX_B_BYTES;      // 61440
+constexpr int MX_SMEM = MX_STAGES * MX_STAGE_BYTES + 1024 + 256;
+constexpr int MX_THREADS = 192;
+constexpr uint32_t MX_TMEM_COLS = 512;
+constexpr unsigned long long MX_TIMEOUT_NS = 2000000000ull;
+
+enum { MODE_TRAIL = 0, MODE_PANEL = 1 };
+enum { ERR_TMA_WAIT = 11, ERR_MMA_WAIT = 12, ERR_ACC_WAIT = 13, ERR_EPI_WAIT = 14 };
+
+struct MixedMaps {
+  CUtensorMap panel_a;   // panel slices, box 16 x 128 rows x 10 planes
+  CUtensorMap panel_b;   // panel slices, box 16 x 64 rows x 10 planes
+  CUtensorMap linv_b;    // inverse-diagonal slices, box 16 x 64 rows x 10 planes
+  int64_t* d_prefix = nullptr;   // [max_nt][P+1] tile prefix (trail), then [max_nt][P+1] (panel)
+  int max_nt = 0, P = 0;
+  std::vector<int64_t> h_trail_total, h_panel_total;
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the deadline passed or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(a, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(a, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > MX_TIMEOUT_NS) return false;
+    }
+  }
+}
+// Wait bounded by the deadline only (used to drain work this CTA issued).
+__device__ __forceinline__ bool mbar_wait_deadline(uint32_t a, uint32_t parity) {
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(a, parity)) return true;
+    if ((it & 255u) == 255u && globaltimer() - t0 > MX_TIMEOUT_NS) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 32-byte swizzle, 8-row
+// groups 256 bytes apart (SBO), leading offset unused (K of one MMA fits the
+// 32-byte swizzle width).
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);            // start address
+  d |= (uint64_t)1 << 16;                               // leading byte offset (16 B, unused)
+  d |= (uint64_t)(256 >> 4) << 32;                      // stride byte offset
+  d |= (uint64_t)1 << 46;                               // descriptor version (sm_100 family)
+  d |= (uint64_t)6 << 61;                               // swizzle mode: 32 B
+  return d;
+}
+// Instruction descriptor: bf16 x bf16 -> fp32, K-major A and B, M = 128, N = 64.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t negate_a) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (negate_a << 13) | ((uint32_t)(MX_N >> 3) << 17) |
+         ((uint32_t)(MX_M >> 4) << 24);
+}
+
+// ---------------------------------------------------------------------------
+// tile decoding
+// ---------------------------------------------------------------------------
+struct TileJob {
+  int p, i, j, h;   // problem, output block row, block column (trail: j; panel: k), half
+  bool valid;
+};
+
+__device__ __forceinline__ TileJob decode_tile(const BatchView& v, const int64_t* prefix, int64_t t, int k,
+                                               int mode) {
+  TileJob jb{0, 0, 0, 0, false};
+  // binary search in prefix[0..P]
+  int lo = 0, hi = v.P;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= t) lo = mid; else hi = mid;
+  }
+  const int p = lo;
+  int64_t u = t - prefix[p];
+  const Prob pr = v.prob[p];
+  if (v.status[p] > 0) return jb;
+  jb.p = p;
+  jb.h = (int)(u & 1);
+  u >>= 1;
+  if (mode == MODE_TRAIL) {
+    int a = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+    while ((int64_t)a * (a + 1) / 2 > u) --a;
+    while ((int64_t)(a + 1) * (a + 2) / 2 <= u) ++a;
+    int b = (int)(u - (int64_t)a * (a + 1) / 2);
+    jb.i = k + 1 + a;
+    jb.j = k + 1 + b;
+  } else {
+    jb.i = k + 1 + (int)u;
+    jb.j = k;
+  }
+  jb.valid = jb.i < pr.nt;
+  return jb;
+}
+
+// ---------------------------------------------------------------------------
+// the slice GEMM
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(MX_THREADS, 1)
+    slice_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                      BatchView v, const int64_t* __restrict__ prefix, int64_t ntiles, int k) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + MX_STAGES * MX_STAGE_BYTES);
+  // bars[0..2] full, [3..5] empty, [6] acc_full, [7] acc_empty, [8] drain
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 10);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 11);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (3 + s); };
+  const uint32_t acc_full = bar0 + 8u * 6, acc_empty = bar0 + 8u * 7, drain = bar0 + 8u * 8;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MX_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 128);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    prefetch_map(&map_a);
+    prefetch_map(&map_b);
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(MX_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        TileJob jb = decode_tile(v, prefix, t, k, MODE);
+        if (!jb.valid) continue;
+        const Prob pr = v.prob[jb.p];
+        const int a_row = (int)(pr.row_off + (int64_t)jb.i * BEOR_TB);
+        const int b_row = MODE == MODE_TRAIL ? (int)(pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N)
+                                             : jb.p * BEOR_TB + jb.h * MX_N;
+        for (int kc = 0; kc < BEOR_TB / MX_KC; ++kc, ++it) {
+          const int s = it % MX_STAGES;
+          const uint32_t ph = (it / MX_STAGES) & 1;
+          if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag)) {
+            atomicExch(&v.flags->error, ERR_TMA_WAIT);
+            *abort_flag = 1;
+            goto producer_done;
+          }
+          mbar_expect_tx(full_bar(s), MX_STAGE_BYTES);
+          const uint32_t dst = sbase + s * MX_STAGE_BYTES;
+          tma_load_3d(dst, &map_a, kc * MX_KC, a_row, 0, full_bar(s));
+          tma_load_3d(dst + MX_A_BYTES, &map_b, kc * MX_KC, b_row, 0, full_bar(s));
+        }
+      }
+    producer_done:
+      // drain: every issued copy must have landed before the CTA may exit
+      for (uint32_t q = (it >= MX_STAGES ? it - MX_STAGES : 0); q < it; ++q)
+        mbar_wait_deadline(full_bar(q % MX_STAGES), (q / MX_STAGES) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t it = 0, tcount = 0;
+      constexpr uint32_t ID_POS = idesc_bf16(0), ID_NEG = idesc_bf16(1);
+      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        TileJob jb = decode_tile(v, prefix, t, k, MODE);
+        if (!jb.valid) continue;
+        if (!mbar_wait(acc_empty, (tcount & 1) ^ 1, abort_flag)) {
+          atomicExch(&v.flags->error, ERR_ACC_WAIT);
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        bool bad = false;
+        for (int kc = 0; kc < BEOR_TB / MX_KC; ++kc, ++it) {
+          const int s = it % MX_STAGES;
+          const uint32_t ph = (it / MX_STAGES) & 1;
+          if (!mbar_wait(full_bar(s), ph, abort_flag)) {
+            atomicExch(&v.flags->error, ERR_MMA_WAIT);
+            *abort_flag = 1;
+            bad = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = sbase + s * MX_STAGE_BYTES, b0 = a0 + MX_A_BYTES;
+          // plane p = slice*2 + part (0 re, 1 im)
+#pragma unroll
+          for (int sa = 0; sa < BEOR_NSLICE; ++sa) {
+#pragma unroll
+            for (int sb = 0; sb < BEOR_NSLICE - sa; ++sb) {
+              const int lvl = (sa + sb) < 2 ? (sa + sb) : 2;
+              const uint32_t d_re = tmem + (uint32_t)(lvl * 2 + 0) * MX_N;
+              const uint32_t d_im = tmem + (uint32_t)(lvl * 2 + 1) * MX_N;
+              // first contribution to each accumulator of a tile overwrites it
+              // (loop order: the first pair of every level has sa == 0)
+              const uint32_t acc0 = (kc == 0 && sa == 0 && sb <= 2) ? 0u : 1u;
+              const uint64_t ar = sdesc_sw32(a0 + (sa * 2 + 0) * (MX_M * 32));
+              const uint64_t ai = sdesc_sw32(a0 + (sa * 2 + 1) * (MX_M * 32));
+              const uint64_t br = sdesc_sw32(b0 + (sb * 2 + 0) * (MX_N * 32));
+              const uint64_t bi = sdesc_sw32(b0 + (sb * 2 + 1) * (MX_N * 32));
+              tc_mma(d_re, ar, br, ID_POS, acc0);
+              tc_mma(d_re, ai, bi, ID_POS, 1u);
+              tc_mma(d_im, ai, br, ID_POS, acc0);
+              tc_mma(d_im, ar, bi, ID_NEG, 1u);
+            }
+          }
+          tc_commit(empty_bar(s));
+        }
+        if (bad) break;
+        tc_commit(acc_full);
+        ++tcount;
+      }
+      // drain outstanding tensor-core work before TMEM is released
+      tc_commit(drain);
+      mbar_wait_deadline(drain, 0);
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int lane_base = 32 * (warp & 3);
+    const int r = lane_base + lane;   // output row within the tile
+    uint32_t tcount = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      TileJob jb = decode_tile(v, prefix, t, k, MODE);
+      if (!jb.valid) continue;
+      if (!mbar_wait(acc_full, tcount & 1, abort_flag)) {
+        atomicExch(&v.flags->error, ERR_EPI_WAIT);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const Prob pr = v.prob[jb.p];
+      const int e_r = v.panel_exp[pr.row_off + (int64_t)jb.i * BEOR_TB + r];
+      const int32_t* ecol = MODE == MODE_TRAIL ? v.panel_exp + pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N
+                                               : v.linv_exp + (int64_t)jb.p * BEOR_TB + jb.h * MX_N;
+      const int out_j = MODE == MODE_TRAIL ? jb.j : k;
+      float4* C = reinterpret_cast<float4*>(v.ws) + pr.ws_off + tri_index(jb.i, out_j) * BEOR_TILE_ELEMS +
+                  (int64_t)(jb.h * MX_N) * BEOR_TB + r;
+      const uint32_t trow = tmem + ((uint32_t)lane_base << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < MX_N; c0 += 16) {
+        float a0r[16], a0i[16], a1r[16], a1i[16], a2r[16], a2i[16];
+        tmem_ld16(trow + 0 * MX_N + c0, a0r);
+        tmem_ld16(trow + 1 * MX_N + c0, a0i);
+        tmem_ld16(trow + 2 * MX_N + c0, a1r);
+        tmem_ld16(trow + 3 * MX_N + c0, a1i);
+        tmem_ld16(trow + 4 * MX_N + c0, a2r);
+        tmem_ld16(trow + 5 * MX_N + c0, a2i);
+        tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int c = c0 + q;
+          const int ec = __ldg(ecol + c);
+          int ex = e_r + ec - 14;
+          if (e_r <= -1000 || ec <= -1000) ex = 0;
+          ex = max(-250, min(250, ex));
+          const int e1 = ex >> 1, e2 = ex - e1;   // two exact power-of-two factors
+          const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
+          dfl vr = df_add(df_two_sum(a0r[q], a1r[q]), dfl{a2r[q], 0.0f});
+          dfl vi = df_add(df_two_sum(a0i[q], a1i[q]), dfl{a2i[q], 0.0f});
+          vr.hi = vr.hi * s1 * s2; vr.lo = vr.lo * s1 * s2;
+          vi.hi = vi.hi * s1 * s2; vi.lo = vi.lo * s1 * s2;
+          float4* cp = C + (int64_t)c * BEOR_TB;
+          if (MODE == MODE_TRAIL) {
+            float4 w = *cp;
+            dfl wr = df_add(dfl{w.x, w.y}, df_neg(vr));
+            dfl wi = df_add(dfl{w.z, w.w}, df_neg(vi));
+            *cp = make_float4(wr.hi, wr.lo, wi.hi, wi.lo);
+          } else {
+            *cp = make_float4(vr.hi, vr.lo, vi.hi, vi.lo);
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(acc_empty);
+      ++tcount;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MX_TMEM_COLS));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// slicing of the panel rows: rows of tiles (i, k), i > k, of every problem
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) slice_panel_kernel(BatchView v, int k) {
+  constexpr int R = 16;                     // rows per block
+  __shared__ float4 s[BEOR_TB][R + 1];      // [column][row], padded
+  const int p = blockIdx.y;
+  const Prob pr = v.prob[p];
+  const int i = k + 1 + blockIdx.x / (BEOR_TB / R);
+  if (i >= pr.nt || v.status[p] > 0) return;
+  const int r0 = (blockIdx.x % (BEOR_TB / R)) * R;
+  const float4* tile = reinterpret_cast<const float4*>(v.ws) + pr.ws_off + tri_index(i, k) * BEOR_TILE_ELEMS;
+  for (int e = threadIdx.x; e < BEOR_TB * R; e += 256) {
+    int c = e / R, r = e % R;
+    s[c][r] = tile[c * BEOR_TB + r0 + r];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t rows = v.rows;
+  for (int r = warp; r < R; r += 8) {
+    float mx = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float4 a = s[lane + 32 * q][r];
+      mx = fmaxf(mx, fmaxf(fabsf(a.x), fabsf(a.z)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = mx > 0.0f ? ilogbf(mx) + 1 : -1000;
+    const int64_t grow = pr.row_off + (int64_t)i * BEOR_TB + r0 + r;
+    if (lane == 0) v.panel_exp[grow] = e;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 a = s[lane + 32 * q][r];
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        const float hi = part ? a.z : a.x, lo = part ? a.w : a.y;
+        // balanced base-256 digits of the fixed-point number round(x * 2^(39 - e))
+        long long X = 0;
+        if (e > -1000) X = llrintf(ldexpf(hi, 39 - e)) + llrintf(ldexpf(lo, 39 - e));
+        int dg[BEOR_NSLICE];
+#pragma unroll
+        for (int sl = BEOR_NSLICE - 1; sl >= 1; --sl) {
+          const long long m = ((X + 128) & 255) - 128;
+          dg[sl] = (int)m;
+          X = (X - m) >> 8;
+        }
+        dg[0] = (int)X;
+#pragma unroll
+        for (int sl = 0; sl < BEOR_NSLICE; ++sl) {
+          __nv_bfloat16* dst = v.panel_sl + ((int64_t)(sl * 2 + part) * rows + grow) * BEOR_TB + lane + 32 * q;
+          *dst = __float2bfloat16_rn(ldexpf((float)dg[sl], -8 * sl));
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_slice_panel(const BatchView& v, int k, cudaStream_t s) {
+  const int nblk = 8 * (v.max_nt - 1 - k);
+  if (nblk <= 0) return cudaSuccess;
+  slice_panel_kernel<<<dim3(nblk, v.P), 256, 0, s>>>(v, k);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// host side: tensor maps, tile prefixes, launches
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static cudaError_t make_map(CUtensorMap* m, void* base, int64_t rows, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t dims[3] = {(cuuint64_t)BEOR_TB, (cuuint64_t)rows, (cuuint64_t)BEOR_NPLANE};
+  cuuint64_t strides[2] = {(cuuint64_t)BEOR_TB * 2, (cuuint64_t)rows * BEOR_TB * 2};
+  cuuint32_t box[3] = {(cuuint32_t)MX_KC, (cuuint32_t)box_rows, (cuuint32_t)BEOR_NPLANE};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t mixed_maps_create(const BatchView& v, MixedMaps** out) {
+  *out = nullptr;
+  MixedMaps* m = new MixedMaps();
+  cudaError_t e = make_map(&m->panel_a, v.panel_sl, v.rows, MX_M);
+  if (e == cudaSuccess) e = make_map(&m->panel_b, v.panel_sl, v.rows, MX_N);
+  if (e == cudaSuccess) e = make_map(&m->linv_b, v.linv_sl, (int64_t)v.P * BEOR_TB, MX_N);
+  if (e != cudaSuccess) {
+    delete m;
+    return e;
+  }
+  // tile prefix sums per step for both modes
+  std::vector<Prob> hp(v.P);
+  e = cudaMemcpy(hp.data(), v.prob, sizeof(Prob) * v.P, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    delete m;
+    return e;
+  }
+  m->max_nt = v.max_nt;
+  m->P = v.P;
+  std::vector<int64_t> pre((size_t)2 * v.max_nt * (v.P + 1), 0);
+  m->h_trail_total.assign(v.max_nt, 0);
+  m->h_panel_total.assign(v.max_nt, 0);
+  for (int k = 0; k < v.max_nt; ++k) {
+    int64_t* tr = pre.data() + (size_t)k * (v.P + 1);
+    int64_t* pa = pre.data() + (size_t)(v.max_nt + k) * (v.P + 1);
+    for (int p = 0; p < v.P; ++p) {
+      int64_t T = std::max(0, hp[p].nt - k - 1);
+      tr[p + 1] = tr[p] + tri_count((int)T) * 2;
+      pa[p + 1] = pa[p] + T * 2;
+    }
+    m->h_trail_total[k] = tr[v.P];
+    m->h_panel_total[k] = pa[v.P];
+  }
+  e = cudaMalloc(&m->d_prefix, sizeof(int64_t) * pre.size());
+  if (e == cudaSuccess) e = cudaMemcpy(m->d_prefix, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (m->d_prefix) cudaFree(m->d_prefix);
+    delete m;
+    return e;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(slice_gemm_kernel<MODE_TRAIL>, cudaFuncAttributeMaxDynamicSharedMemorySize, MX_SMEM);
+    cudaFuncSetAttribute(slice_gemm_kernel<MODE_PANEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, MX_SMEM);
+    attr = true;
+  }
+  *out = m;
+  return cudaSuccess;
+}
+
+void mixed_maps_destroy(MixedMaps* m) {
+  if (!m) return;
+  if (m->d_prefix) cudaFree(m->d_prefix);
+  delete m;
+}
+
+static int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+cudaError_t launch_panel_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s) {
+  const int64_t nt = m->h_panel_total[k];
+  if (nt <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>(nt, num_sms());
+  const int64_t* pre = m->d_prefix + (size_t)(m->max_nt + k) * (m->P + 1);
+  slice_gemm_kernel<MODE_PANEL><<<grid, MX_THREADS, MX_SMEM, s>>>(m->panel_a, m->linv_b, v, pre, nt, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trail_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s) {
+  const int64_t nt = m->h_trail_total[k];
+  if (nt <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>(nt, num_sms());
+  const int64_t* pre = m->d_prefix + (size_t)k * (m->P + 1);
+  slice_gemm_kernel<MODE_TRAIL><<<grid, MX_THREADS, MX_SMEM, s>>>(m->panel_a, m->panel_b, v, pre, nt, k);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// float64 refinement: vec_r = dbar - (M + diag Phi^-1) x, x += vec_d
+// ---------------------------------------------------------------------------
+__global__ void resid_init_kernel(BatchView v) {
+  const int p = blockIdx.y;
+  const Prob pr = v.prob[p];
+  const SetDesc sd = v.sets[pr.set];
+  const int np = pr.nt * BEOR_TB;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += gridDim.x * blockDim.x) {
+    double2 x = v.vec_x[pr.row_off + j], d = sd.dbar[j];
+    double w = v.phi_inv[pr.row_off + j];
+    v.vec_r[pr.row_off + j] = j < pr.n ? make_double2(d.x - w * x.x, d.y - w * x.y) : make_double2(0.0, 0.0);
+  }
+}
+
+// One CTA per (lower tile of M, problem): r_I -= M_IJ x_J and, off the
+// diagonal, r_J -= M_IJ^H x_I, accumulated with float64 atomics.
+__global__ void __launch_bounds__(128) resid_tile_kernel(BatchView v) {
+  __shared__ double2 xj[BEOR_TB], xi[BEOR_TB];
+  const int p = blockIdx.y;
+  const Prob pr = v.prob[p];
+  const SetDesc sd = v.sets[pr.set];
+  const int64_t t = blockIdx.x;
+  if (t >= tri_count(pr.nt) || v.status[p] > 0) return;
+  int I, J;
+  {
+    int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((int64_t)a * (a + 1) / 2 > t) --a;
+    while ((int64_t)(a + 1) * (a + 2) / 2 <= t) ++a;
+    I = a;
+    J = (int)(t - (int64_t)a * (a + 1) / 2);
+  }
+  const double2* Mt = sd.M + t * BEOR_TILE_ELEMS;
+  const double2* x = v.vec_x + pr.row_off;
+  double2* r = v.vec_r + pr.row_off;
+  const int tid = threadIdx.x;
+  xj[tid] = x[J * BEOR_TB + tid];
+  xi[tid] = x[I * BEOR_TB + tid];
+  __syncthreads();
+  // rows of block I
+  double sr = 0.0, si = 0.0;
+  for (int c = 0; c < BEOR_TB; ++c) {
+    double2 m = Mt[c * BEOR_TB + tid], q = xj[c];
+    if (I == J && c > tid) {   // upper part of a diagonal tile: use the Hermitian mirror
+      double2 mm = Mt[tid * BEOR_TB + c];
+      m = make_double2(mm.x, -mm.y);
+    }
+    sr = fma(m.x, q.x, fma(-m.y, q.y, sr));
+    si = fma(m.x, q.y, fma(m.y, q.x, si));
+  }
+  atomicAdd(&r[I * BEOR_TB + tid].x, -sr);
+  atomicAdd(&r[I * BEOR_TB + tid].y, -si);
+  if (I != J) {
+    // rows of block J: (M_IJ^H x_I)[c] = sum_r conj(M[r][c]) x_I[r]; one warp per column
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int c = warp; c < BEOR_TB; c += 4) {
+      double ar = 0.0, ai = 0.0;
+      for (int rr = lane; rr < BEOR_TB; rr += 32) {
+        double2 m = Mt[c * BEOR_TB + rr], q = xi[rr];
+        ar = fma(m.x, q.x, fma(m.y, q.y, ar));
+        ai = fma(m.x, q.y, fma(-m.y, q.x, ai));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+      }
+      if (lane == 0) {
+        atomicAdd(&r[J * BEOR_TB + c].x, -ar);
+        atomicAdd(&r[J * BEOR_TB + c].y, -ai);
+      }
+    }
+  }
+}
+
+__global__ void resid_norm_kernel(BatchView v) {
+  const int p = blockIdx.x;
+  const Prob pr = v.prob[p];
+  const SetDesc sd = v.sets[pr.set];
+  __shared__ double red[2][32];
+  double a = 0.0, b = 0.0;
+  for (int j = threadIdx.x; j < pr.n; j += blockDim.x) {
+    double2 r = v.vec_r[pr.row_off + j], d = sd.dbar[j];
+    a += r.x * r.x + r.y * r.y;
+    b += d.x * d.x + d.y * d.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sa += red[0][w];
+      sb += red[1][w];
+    }
+    double rel = sb > 0.0 ? sqrt(sa / sb) : 0.0;
+    v.resid[p] = rel;
+    if (v.status[p] == 0 && !(rel <= 1e-10)) v.status[p] = -1;
+    if (v.status[p] == -1 && rel <= 1e-10) v.status[p] = 0;
+  }
+}
+
+cudaError_t launch_residual(const BatchView& v, cudaStream_t s) {
+  resid_init_kernel<<<dim3(8, v.P), 256, 0, s>>>(v);
+  int64_t tiles = tri_count(v.max_nt);
+  resid_tile_kernel<<<dim3((unsigned)tiles, v.P), 128, 0, s>>>(v);
+  resid_norm_kernel<<<v.P, 256, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+__global__ void refine_update_kernel(BatchView v) {
+  const int p = blockIdx.y;
+  const Prob pr = v.prob[p];
+  if (v.status[p] > 0) return;
+  const int np = pr.nt * BEOR_TB;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += gridDim.x * blockDim.x) {
+    double2 x = v.vec_x[pr.row_off + j], d = v.vec_d[pr.row_off + j];
+    v.vec_x[pr.row_off + j] = make_double2(x.x + d.x, x.y + d.y);
+  }
+}
+
+cudaError_t launch_refine_update(const BatchView& v, cudaStream_t s) {
+  refine_update_kernel<<<dim3(8, v.P), 256, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+int mixed_supported(int device) {
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+  if (major != 10 || minor != 3) return 0;
+  return get_encode() != nullptr;
+}
+
 }  // namespace beor

@@ -1,0 +1,72 @@
+"""GPU mixed-precision path (bf16 slice products on tcgen05, double-float
+working matrix, float64 diagonal blocks and refinement) against the CPU oracle.
+
+Tolerances: |lnL - lnL_oracle| <= 1e-2 absolute and
+||abar - abar_oracle|| / ||abar_oracle|| <= 1e-6.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth.instrument import random_problem
+from tests.gpu_common import make_like, oracle_eval, phis
+
+pytestmark = pytest.mark.gpu
+
+ATOL_LNL = 1e-2
+RTOL_ABAR = 1e-6
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2501_12928_gb300 as P
+    return P
+
+
+def test_mixed_C0(P):
+    lk = make_like(P, "C0", precision="mixed")
+    ph = phis("C0", 16, stream=41)
+    got, st = lk.lnl(ph)
+    ref = np.array([oracle_eval("C0", p)["lnl"] for p in ph])
+    assert np.all(st == 0), st
+    err = np.abs(got - ref)
+    print("C0 mixed max |dlnL|", err.max(), lk.stats())
+    assert err.max() <= ATOL_LNL
+
+
+def test_mixed_posterior_mean_C0(P):
+    lk = make_like(P, "C0", precision="mixed")
+    for p in phis("C0", 3, stream=43):
+        a, st = lk.posterior_mean(p)
+        ref = oracle_eval("C0", p)["abar"]
+        assert st == 0
+        assert np.linalg.norm(a - ref) <= RTOL_ABAR * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("nvis,n,nk", [(12, 5, 2), (300, 130, 3), (400, 383, 5), (700, 640, 4)])
+def test_mixed_random_shapes(P, nvis, n, nk):
+    p = random_problem(nvis, n, nk, seed=n + 1)
+    lk = P.Likelihood("mixed")
+    lk.set_T(p["T"], p["kbin"], nk, 2.0)
+    lk.set_data(p["d"], p["noise_var"])
+    lk.precompute()
+    M = O.herm_dense(p["T"], p["noise_var"])
+    db = O.dbar_dense(p["T"], p["noise_var"], p["d"])
+    ph = np.random.default_rng(n).uniform(-2, 2, (4, nk))
+    got, st = lk.lnl(ph)
+    for i in range(4):
+        r = O.evaluate(M, db, p["kbin"], ph[i], 2.0)
+        assert st[i] == 0 and abs(got[i] - r["lnl"]) <= ATOL_LNL, (i, got[i], r["lnl"])
+    a, st0 = lk.posterior_mean(ph[0])
+    ref = O.evaluate(M, db, p["kbin"], ph[0], 2.0)["abar"]
+    assert np.linalg.norm(a - ref) <= RTOL_ABAR * np.linalg.norm(ref)
+
+
+def test_mixed_matches_fp64_gpu_C0(P):
+    a = make_like(P, "C0", precision="mixed")
+    b = make_like(P, "C0", precision="fp64")
+    ph = phis("C0", 8, stream=47)
+    la, _ = a.lnl(ph)
+    lb, _ = b.lnl(ph)
+    assert np.abs(la - lb).max() <= ATOL_LNL
