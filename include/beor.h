@@ -142,6 +142,11 @@ int beor_get_stats(const beor_ctx *ctx, beor_stats *out);
 int beor_get_terms(const beor_ctx *ctx, double *logdet_phi, double *logdet_sigma, double *q,
                    int B);
 
+/* Cholesky factor L (n_model x n_model, lower, row-major, host memory) of
+ * prior point b of the last beor_lnl call on ctx, as left in the working
+ * matrix by the factorisation (diagnostics and tests). */
+int beor_get_factor(const beor_ctx *ctx, int b, beor_c128 *L_out);
+
 /* ---------------------------------------------------------------------
  * Learned emulator of lnL(phi) (pre-screening for the nested sampler).
  * A multilayer perceptron n_in -> depth x width GELU -> 1 with bf16 weights

@@ -48,6 +48,7 @@ def _load():
         "beor_get_dbar": [_P, _P],
         "beor_get_stats": [_P, _P],
         "beor_get_terms": [_P, _P, _P, _P, _c.c_int],
+        "beor_get_factor": [_P, _c.c_int, _P],
         "beor_mlp_create": [_c.POINTER(_P), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64],
         "beor_mlp_destroy": [_P],
         "beor_mlp_set_norm": [_P, _P, _P, _c.c_float, _c.c_float],
@@ -207,6 +208,13 @@ class Likelihood:
         st = _Stats()
         _check(_lib().beor_get_stats(self._h, ctypes.byref(st)), "beor_get_stats")
         return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def factor(self, b: int = 0):
+        """Cholesky factor of prior point b of the last lnl() call (host copy)."""
+        n = self.dims()[1]
+        L = np.empty((n, n), np.complex128)
+        _check(_lib().beor_get_factor(self._h, b, ctypes.c_void_p(L.ctypes.data)), "beor_get_factor")
+        return L
 
     def terms(self, B: int):
         a, b, c = (np.empty(B, np.float64) for _ in range(3))

@@ -688,4 +688,37 @@ int beor_get_terms(const beor_ctx* c, double* logdet_phi, double* logdet_sigma, 
   return BEOR_OK;
 }
 
+int beor_get_factor(const beor_ctx* c, int b, beor_c128* L_out) {
+  if (!c || !c->last_plan || !L_out) return BEOR_EINVAL;
+  Plan* pl = c->last_plan;
+  const int p = c->last_first + b;
+  if (b < 0 || p >= pl->P || pl->h_prob[p].set != pl->h_prob[c->last_first].set) return BEOR_EINVAL;
+  cudaSetDevice(c->device);
+  const Prob& pr = pl->h_prob[p];
+  const size_t ntile = (size_t)tri_count(pr.nt) * BEOR_TILE_ELEMS;
+  std::vector<double2> t(ntile);
+  if (pl->mixed) {
+    std::vector<float4> f(ntile);
+    CKC(nullptr, cudaMemcpy(f.data(), reinterpret_cast<float4*>(pl->view.ws) + pr.ws_off, sizeof(float4) * ntile,
+                            cudaMemcpyDeviceToHost));
+    for (size_t e = 0; e < ntile; ++e)
+      t[e] = make_double2((double)f[e].x + (double)f[e].y, (double)f[e].z + (double)f[e].w);
+  } else {
+    CKC(nullptr, cudaMemcpy(t.data(), reinterpret_cast<double2*>(pl->view.ws) + pr.ws_off, sizeof(double2) * ntile,
+                            cudaMemcpyDeviceToHost));
+  }
+  const int64_t n = pr.n;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      double2 v = make_double2(0.0, 0.0);
+      if (j <= i) {
+        int I = (int)(i / BEOR_TB), J = (int)(j / BEOR_TB);
+        v = t[(size_t)(tri_index(I, J) * BEOR_TILE_ELEMS + (j % BEOR_TB) * BEOR_TB + (i % BEOR_TB))];
+      }
+      L_out[i * n + j].re = v.x;
+      L_out[i * n + j].im = v.y;
+    }
+  return BEOR_OK;
+}
+
 }  // extern "C"

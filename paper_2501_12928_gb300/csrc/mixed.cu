@@ -8,9 +8,11 @@
 // sigma_s * 2^(-8 s).  A product of two slices is exact in fp32, and a sum of
 // 256 of them (one 128-complex block column, real and imaginary parts) stays
 // below 2^24 units, so the fp32 accumulator of the tensor core is exact for
-// the level-0 pair (0,0) and the level-1 pairs (0,1), (1,0).  All pairs with
-// s + t >= 2 share a third accumulator whose rounding lies 2^-16 below the
-// leading term.  The epilogue adds the three levels as a double-float number,
+// the level-0 pair (0,0), the level-1 pairs (0,1), (1,0) and the level-2
+// pairs (0,2), (1,1), (2,0) (at most 1.26e7 units of 2^-16).  All pairs with
+// s + t >= 3 share a fourth accumulator whose rounding error (about 2^-19 of
+// its size after ~1500 fp32 additions) lies about 2^-39 below the leading
+// term.  The epilogue adds the four levels as a double-float number,
 // scales by 2^(e_r + e_c - 14) and updates the working matrix, itself kept as
 // a double-float pair per real number.  The result is accurate to about
 // 2^-40 of the operand row scales, which keeps log|Sigma| well inside the
@@ -21,7 +23,8 @@
 // x 64 complex columns): warp 0 issues TMA loads of the slice planes into a
 // 3-stage shared-memory ring (32-byte swizzle, K chunks of 16), warp 1 issues
 // the tcgen05.mma instructions (M = 128, N = 64, K = 16, bf16 -> fp32) into
-// six TMEM accumulators (3 levels x re/im), warps 2-5 drain TMEM and apply
+// eight TMEM accumulators (4 levels x re/im, all 512 columns), warps 2-5 drain
+// TMEM and apply
 // the update.  Every wait is bounded by a %globaltimer deadline; on expiry
 // the kernel records an error code, drains what it issued and returns.
 #include <cuda.h>
@@ -307,12 +310,12 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           for (int sa = 0; sa < BEOR_NSLICE; ++sa) {
 #pragma unroll
             for (int sb = 0; sb < BEOR_NSLICE - sa; ++sb) {
-              const int lvl = (sa + sb) < 2 ? (sa + sb) : 2;
+              const int lvl = (sa + sb) < 3 ? (sa + sb) : 3;
               const uint32_t d_re = tmem + (uint32_t)(lvl * 2 + 0) * MX_N;
               const uint32_t d_im = tmem + (uint32_t)(lvl * 2 + 1) * MX_N;
               // first contribution to each accumulator of a tile overwrites it
               // (loop order: the first pair of every level has sa == 0)
-              const uint32_t acc0 = (kc == 0 && sa == 0 && sb <= 2) ? 0u : 1u;
+              const uint32_t acc0 = (kc == 0 && sa == 0 && sb <= 3) ? 0u : 1u;
               const uint64_t ar = sdesc_sw32(a0 + (sa * 2 + 0) * (MX_M * 32));
               const uint64_t ai = sdesc_sw32(a0 + (sa * 2 + 1) * (MX_M * 32));
               const uint64_t br = sdesc_sw32(b0 + (sb * 2 + 0) * (MX_N * 32));
@@ -357,13 +360,15 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       const uint32_t trow = tmem + ((uint32_t)lane_base << 16);
 #pragma unroll 1
       for (int c0 = 0; c0 < MX_N; c0 += 16) {
-        float a0r[16], a0i[16], a1r[16], a1i[16], a2r[16], a2i[16];
+        float a0r[16], a0i[16], a1r[16], a1i[16], a2r[16], a2i[16], a3r[16], a3i[16];
         tmem_ld16(trow + 0 * MX_N + c0, a0r);
         tmem_ld16(trow + 1 * MX_N + c0, a0i);
         tmem_ld16(trow + 2 * MX_N + c0, a1r);
         tmem_ld16(trow + 3 * MX_N + c0, a1i);
         tmem_ld16(trow + 4 * MX_N + c0, a2r);
         tmem_ld16(trow + 5 * MX_N + c0, a2i);
+        tmem_ld16(trow + 6 * MX_N + c0, a3r);
+        tmem_ld16(trow + 7 * MX_N + c0, a3i);
         tmem_ld_wait();
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -374,8 +379,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           ex = max(-250, min(250, ex));
           const int e1 = ex >> 1, e2 = ex - e1;   // two exact power-of-two factors
           const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
-          dfl vr = df_add(df_two_sum(a0r[q], a1r[q]), dfl{a2r[q], 0.0f});
-          dfl vi = df_add(df_two_sum(a0i[q], a1i[q]), dfl{a2i[q], 0.0f});
+          dfl vr = df_add(df_two_sum(a0r[q], a1r[q]), df_two_sum(a2r[q], a3r[q]));
+          dfl vi = df_add(df_two_sum(a0i[q], a1i[q]), df_two_sum(a2i[q], a3i[q]));
           vr.hi = vr.hi * s1 * s2; vr.lo = vr.lo * s1 * s2;
           vi.hi = vi.hi * s1 * s2; vi.lo = vi.lo * s1 * s2;
           float4* cp = C + (int64_t)c * BEOR_TB;
