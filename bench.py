@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Exact lnL evaluations per second at N_model ~ 11k on one GB300.
+
+Workload: three sub-band instruments on one uv grid (n_f = 24, 32, 48
+channels; N_model = 6048, 7840, 11424; 331 baselines x 16 times), B = 16
+prior points each, all 48 factorised in one batched evaluation (one graph
+launch).  A step is one such evaluation.  The mixed-precision path is timed;
+the float64 GPU path is timed on one point per sub-band for the comparison,
+and the CPU oracle on a bounded sample for the host baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank evaluates its own replica of the workload
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SUBBANDS = ("C3_24", "C3_32", "C3_48")
+METRIC = "exact lnL evals/s at N_model~11k (C3 sub-band mix, mixed precision)"
+UNIT = "evals/s"
+# bf16 tensor operations of one trailing-update output tile (128 x 64 complex,
+# K = 128 complex): 15 slice pairs x 4 real products x 8 K-chunks x 2*128*64*16
+TILE_TENSOR_FLOP = 15 * 4 * 8 * 2 * 128 * 64 * 16
+TILE_USEFUL_FLOP = 8 * 128 * 64 * 128      # the complex GEMM it computes
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def build_workload(B: int):
+    from synth import build_instrument, draw_phi
+    insts = {}
+    insts["C3_48"] = build_instrument("C3_48")
+    for name in ("C3_24", "C3_32"):
+        insts[name] = build_instrument(name, A_from=insts["C3_48"])
+    phis = {n: draw_phi(insts[n].spec, B) for n in SUBBANDS}
+    return insts, phis
+
+
+def make_likes(P, insts, precision):
+    likes = []
+    for n in SUBBANDS:
+        inst = insts[n]
+        lk = P.Likelihood(precision)
+        lk.set_instrument(inst.A, inst.W, inst.kbin, inst.spec.n_k, inst.spec.lssm_prior_var)
+        lk.set_data(inst.d, inst.noise_var)
+        lk.precompute()
+        likes.append(lk)
+    return likes
+
+
+def trail_tiles_per_step(n_models, B):
+    """Trailing-update tiles of one batched evaluation (all problems, all steps)."""
+    tot = 0
+    for n in n_models:
+        nt = (n + 127) // 128
+        for k in range(nt - 1):
+            T = nt - k - 1
+            tot += B * T * (T + 1)   # T(T+1)/2 block pairs x 2 column halves
+    return tot
+
+
+def cpu_baseline(insts, n_models, reps=1):
+    """The oracle, as it stands, on the host cores: one evaluation of the
+    N = 6048 sub-band, scaled to the sub-band mix by the cubic cost of the
+    Cholesky."""
+    import oracle as O
+    inst = insts["C3_24"]
+    M = O.herm_structured(inst.A, inst.W, inst.noise_var)
+    db = O.dbar_structured(inst.A, inst.W, inst.noise_var, inst.d)
+    from synth import draw_phi
+    phi = draw_phi(inst.spec, reps, stream=9)
+    t0 = time.perf_counter()
+    for p in phi:
+        O.evaluate(M, db, inst.kbin, p, inst.spec.lssm_prior_var)
+    dt = (time.perf_counter() - t0) / reps
+    n0 = inst.spec.n_model
+    mix_time = dt * sum((n / n0) ** 3 for n in n_models) / len(n_models)   # seconds per eval of the mix
+    return {"value": 1.0 / mix_time, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{reps} oracle evaluation(s) at N_model={n0} ({dt:.2f} s each, numpy/BLAS threads = "
+                      f"host cores), scaled to the 6048/7840/11424 mix by (N/{n0})^3"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    insts, _ = build_workload(1)
+    n_models = [insts[n].spec.n_model for n in SUBBANDS]
+    import oracle as O
+    inst = insts["C3_24"]
+    M = O.herm_structured(inst.A, inst.W, inst.noise_var)
+    db = O.dbar_structured(inst.A, inst.W, inst.noise_var, inst.d)
+    from synth import draw_phi
+    phis = draw_phi(inst.spec, args.warmup + args.steps, stream=9)
+    for p in phis[: args.warmup]:
+        O.evaluate(M, db, inst.kbin, p, inst.spec.lssm_prior_var)
+    t0 = time.perf_counter()
+    for p in phis[args.warmup:]:
+        O.evaluate(M, db, inst.kbin, p, inst.spec.lssm_prior_var)
+    dt = (time.perf_counter() - t0) / args.steps
+    scale = sum((n / inst.spec.n_model) ** 3 for n in n_models) / len(n_models)
+    value = 1.0 / (dt * scale)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "C3 sub-band mix (N_model 6048/7840/11424), oracle sample at N=6048"},
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value,
+                             "sample": f"one oracle evaluation at N_model={inst.spec.n_model} per step, "
+                                       "scaled to the mix by (N/6048)^3"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--B", type=int, default=16)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    ws, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import paper_2501_12928_gb300 as P
+
+    insts, phis = build_workload(args.B)
+    n_models = [insts[n].spec.n_model for n in SUBBANDS]
+    t0 = time.perf_counter()
+    likes = make_likes(P, insts, "mixed")
+    torch.cuda.synchronize()
+    t_pre = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    dev_phi = [torch.tensor(phis[n], dtype=torch.float64, device="cuda") for n in SUBBANDS]
+    out = [torch.empty(args.B, dtype=torch.float64, device="cuda") for _ in SUBBANDS]
+    sts = [torch.empty(args.B, dtype=torch.int32, device="cuda") for _ in SUBBANDS]
+    P.set_profiling(True)
+
+    def step():
+        _lnl_multi_dev(P, likes, dev_phi, out, sts)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    trail_ms, trail_n, cls_ms = 0.0, 0, {}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+            st = likes[0].stats()
+            trail_ms += st["ms_class"]["trail"]
+            trail_n += st["n_class"]["trail"]
+            for k, v in st["ms_class"].items():
+                cls_ms[k] = cls_ms.get(k, 0.0) + v
+        e1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    evals_step = args.B * len(SUBBANDS)
+    value = evals_step * args.steps * ws / elapsed
+    launches = likes[0].stats()["kernel_launches"]
+    status_ok = all(int((s != 0).sum().item()) == 0 for s in sts)
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    P.set_profiling(False)
+    host_phi = [np.ascontiguousarray(phis[n]) for n in SUBBANDS]
+    for _ in range(2):
+        P.lnl_multi(likes, host_phi)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        outs, _ = P.lnl_multi(likes, host_phi)
+    t_e2e = time.perf_counter() - t0
+    e2e_value = evals_step * args.steps * ws / t_e2e
+
+    # roofline of the dominant kernel (trailing slice GEMM), timed inside the steps above
+    peaks, peak_src = _peaks()
+    tiles = trail_tiles_per_step(n_models, args.B)
+    trail_s = trail_ms / 1e3 / args.steps
+    achieved = tiles * TILE_TENSOR_FLOP / trail_s / 1e12 if trail_s > 0 else None
+    peak = peaks.get("bf16_tflops_sustained", 1708.8)
+    traffic = _traffic_per_launch(tiles / max(1, trail_n / args.steps))
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "kernel": "slice_gemm_kernel<TRAIL> (bf16 tensor ops of the 5-slice product)",
+            "peak_source": f"bf16 dense sustained, {peak_src}",
+            "useful_tflops": tiles * TILE_USEFUL_FLOP / trail_s / 1e12 if trail_s > 0 else None,
+            "avg_launch_ms": trail_ms / max(1, trail_n)}
+
+    # float64 GPU comparator: one point per sub-band in one batched evaluation
+    fp64 = None
+    if not args.no_fp64:
+        P.set_profiling(False)
+        lf = make_likes(P, insts, "fp64")
+        ph1 = [phis[n][:1] for n in SUBBANDS]
+        P.lnl_multi(lf, ph1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.fp64_steps):
+            P.lnl_multi(lf, ph1)
+        dt = (time.perf_counter() - t0) / args.fp64_steps
+        fp64 = {"value": len(SUBBANDS) / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+                "workload": "one point per sub-band (N 6048/7840/11424) per batched evaluation"}
+        for lk in lf:
+            lk.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(insts, n_models)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 slice products (exact, fp32 accumulate) + double-float / f64",
+            "data": "synthetic",
+            "config": {"workload": "C3: 3 sub-band instruments (n_f 24/32/48, N_model 6048/7840/11424, "
+                                   "331 baselines x 16 times), B=16 each, one batched evaluation per step",
+                       "B_per_subband": args.B, "n_model": n_models, "precompute_s": round(t_pre, 2),
+                       "l2": "inputs larger than L2 (working matrices ~30 GB)", "parallelism": "replicas"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * sum(p.size for p in host_phi),
+                    "d2h_bytes_per_step": 12 * evals_step},
+            "gpu_launches": int(launches) * args.steps,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "fp64_gpu": fp64,
+            "speedup_vs_fp64_gpu": value / fp64["value"] if fp64 else None,
+            "kernel_ms_per_step": {k: v / args.steps for k, v in cls_ms.items()},
+            "status_all_ok": status_ok,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _lnl_multi_dev(P, likes, dev_phi, out, sts):
+    """One batched evaluation with device-resident inputs and outputs."""
+    import ctypes
+    from paper_2501_12928_gb300 import beor as Bm
+    n = len(likes)
+    ctxs = (ctypes.c_void_p * n)(*[lk._h.value for lk in likes])
+    pp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in dev_phi])
+    Bs = (ctypes.c_int * n)(*[t.shape[0] for t in dev_phi])
+    op = (ctypes.c_void_p * n)(*[t.data_ptr() for t in out])
+    sp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in sts])
+    import torch
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    Bm._check(Bm._lib().beor_lnl_multi(ctypes.cast(ctxs, ctypes.c_void_p), n, ctypes.cast(pp, ctypes.c_void_p),
+                                       ctypes.cast(Bs, ctypes.c_void_p), ctypes.cast(op, ctypes.c_void_p),
+                                       ctypes.cast(sp, ctypes.c_void_p), s), "beor_lnl_multi")
+
+
+def _traffic_per_launch(tiles_per_launch):
+    """DRAM bytes per trailing launch from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "slice_gemm_trail_C3.md")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("dram_bytes_per_tile:"):
+                    return float(line.split(":")[1]) * tiles_per_launch
+    except OSError:
+        pass
+    return None
+
+
+if __name__ == "__main__":
+    main()

@@ -128,14 +128,26 @@ int beor_get_model_dims(const beor_ctx *ctx, int64_t *n_vis, int64_t *n_model, i
 int beor_get_M(beor_ctx *ctx, beor_c128 *M_out);
 int beor_get_dbar(beor_ctx *ctx, beor_c128 *dbar_out);
 
-/* Diagnostics of the last lnL / posterior-mean call on this context. */
+/* Diagnostics of the last lnL / posterior-mean call on this context.
+ * ms_class / n_class: device time and launch count per kernel class
+ * (0 prior+init, 1 diagonal block, 2 slicing, 3 panel, 4 trailing update,
+ * 5 triangular solves, 6 refinement residual/update, 7 lnL), filled only
+ * when profiling is on (beor_set_profiling); ms_last is -1 on the call that
+ * captures a batch's graph. */
 typedef struct {
-  int refine_iters_max;     /* largest number of refinement steps taken */
+  int refine_iters_max;     /* refinement steps taken */
   double resid_rel_max;     /* largest final ||dbar - Sigma x|| / ||dbar|| */
   double ms_last;           /* device time of the last batched evaluation */
   int64_t kernel_launches;  /* kernels launched by the last batched evaluation */
+  double ms_class[8];
+  int64_t n_class[8];
 } beor_stats;
 int beor_get_stats(const beor_ctx *ctx, beor_stats *out);
+
+/* Process-wide switch: when on, batched evaluations record a CUDA event
+ * before every kernel (inside the captured graph) and report per-class
+ * device times in beor_stats.  Costs a few microseconds per kernel. */
+int beor_set_profiling(int on);
 
 /* Per-point log-determinant pieces of the last beor_lnl call on ctx (B
  * values each, host memory): log|Phi|, log|Sigma| and q = dbar^H abar. */

@@ -12,4 +12,6 @@ from .beor import (  # noqa: F401
     lnl_multi,
     PREC_FP64,
     PREC_MIXED,
+    KERNEL_CLASSES,
+    set_profiling,
 )

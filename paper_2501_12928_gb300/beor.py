@@ -49,6 +49,7 @@ def _load():
         "beor_get_stats": [_P, _P],
         "beor_get_terms": [_P, _P, _P, _P, _c.c_int],
         "beor_get_factor": [_P, _c.c_int, _P],
+        "beor_set_profiling": [_c.c_int],
         "beor_mlp_create": [_c.POINTER(_P), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64],
         "beor_mlp_destroy": [_P],
         "beor_mlp_set_norm": [_P, _P, _P, _c.c_float, _c.c_float],
@@ -85,7 +86,15 @@ def _check(code, what):
 
 class _Stats(ctypes.Structure):
     _fields_ = [("refine_iters_max", ctypes.c_int), ("resid_rel_max", ctypes.c_double),
-                ("ms_last", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("ms_last", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("ms_class", ctypes.c_double * 8), ("n_class", ctypes.c_int64 * 8)]
+
+
+KERNEL_CLASSES = ("init", "diag", "slice", "panel", "trail", "solve", "refine", "lnl")
+
+
+def set_profiling(on: bool):
+    _check(_lib().beor_set_profiling(1 if on else 0), "beor_set_profiling")
 
 
 def _stream(stream):
@@ -207,7 +216,10 @@ class Likelihood:
     def stats(self) -> dict:
         st = _Stats()
         _check(_lib().beor_get_stats(self._h, ctypes.byref(st)), "beor_get_stats")
-        return {k: getattr(st, k) for k, _ in st._fields_}
+        out = {k: getattr(st, k) for k, _ in st._fields_[:4]}
+        out["ms_class"] = dict(zip(KERNEL_CLASSES, list(st.ms_class)))
+        out["n_class"] = dict(zip(KERNEL_CLASSES, list(st.n_class)))
+        return out
 
     def factor(self, b: int = 0):
         """Cholesky factor of prior point b of the last lnl() call (host copy)."""

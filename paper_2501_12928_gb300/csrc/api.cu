@@ -19,6 +19,9 @@ using namespace beor;
 namespace {
 
 constexpr int kRefineIters = 2;   // refinement steps of the mixed solve (fixed: graph-captured)
+constexpr int kClasses = 8;       // kernel classes timed when profiling is on
+enum { KC_INIT = 0, KC_DIAG, KC_SLICE, KC_PANEL, KC_TRAIL, KC_SOLVE, KC_REFINE, KC_LNL };
+bool g_profiling = false;
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -114,7 +117,11 @@ struct Plan {
   cudaGraph_t graph = nullptr;
   int64_t launches = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool prof = false;
+  std::vector<cudaEvent_t> pev;     // boundary events (profiling)
+  std::vector<int> pcls;            // class of the launch after each boundary event
   ~Plan() {
+    for (cudaEvent_t e : pev) cudaEventDestroy(e);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (maps) mixed_maps_destroy(maps);
@@ -139,51 +146,70 @@ int fail_cuda(beor_ctx* c, cudaError_t e) {
     if (_e != cudaSuccess) return fail_cuda(ctx, _e); \
   } while (0)
 
-// The sequence of kernels of one batched evaluation.
-cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch) {
+// The sequence of kernels of one batched evaluation.  With `mark` set,
+// an externally visible event is recorded before every launch (and one at
+// the end) so that each kernel class can be timed inside the graph.
+cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) {
   const BatchView& v = pl.view;
   int64_t L = 0;
+  size_t ev_i = 0;
   cudaError_t e;
-#define RUN(x)                      \
-  do {                              \
-    e = (x);                        \
-    if (e != cudaSuccess) return e; \
+  if (mark) pl.pcls.clear();
+  auto tick = [&](int cls) -> cudaError_t {
+    if (!mark) return cudaSuccess;
+    if (ev_i >= pl.pev.size()) {
+      cudaEvent_t ev;
+      cudaError_t x = cudaEventCreate(&ev);
+      if (x != cudaSuccess) return x;
+      pl.pev.push_back(ev);
+    }
+    pl.pcls.push_back(cls);
+    return cudaEventRecordWithFlags(pl.pev[ev_i++], s, cudaEventRecordExternal);
+  };
+#define RUN(cls, x)                   \
+  do {                                \
+    e = tick(cls);                    \
+    if (e != cudaSuccess) return e;   \
+    e = (x);                          \
+    if (e != cudaSuccess) return e;   \
   } while (0)
-  RUN(launch_prior_init(v, pl.mixed, s));
+  RUN(KC_INIT, launch_prior_init(v, pl.mixed, s));
   L += 2;
-  RUN(launch_copy_dbar(v, s));
+  RUN(KC_INIT, launch_copy_dbar(v, s));
   L += 1;
   for (int k = 0; k < pl.max_nt; ++k) {
-    RUN(launch_diag(v, k, pl.mixed, s));
+    RUN(KC_DIAG, launch_diag(v, k, pl.mixed, s));
     L += 1;
     if (k + 1 < pl.max_nt) {
       if (pl.mixed) {
-        RUN(launch_slice_panel(v, k, s));
-        RUN(launch_panel_mixed(v, pl.maps, k, s));
-        RUN(launch_slice_panel(v, k, s));
-        RUN(launch_trail_mixed(v, pl.maps, k, s));
+        RUN(KC_SLICE, launch_slice_panel(v, k, s));
+        RUN(KC_PANEL, launch_panel_mixed(v, pl.maps, k, s));
+        RUN(KC_SLICE, launch_slice_panel(v, k, s));
+        RUN(KC_TRAIL, launch_trail_mixed(v, pl.maps, k, s));
         L += 4;
       } else {
-        RUN(launch_panel_f64(v, k, s));
-        RUN(launch_trail_f64(v, k, s));
+        RUN(KC_PANEL, launch_panel_f64(v, k, s));
+        RUN(KC_TRAIL, launch_trail_f64(v, k, s));
         L += 2;
       }
     }
   }
-  RUN(launch_solve(v, pl.mixed, v.vec_b, v.vec_x, s));
+  RUN(KC_SOLVE, launch_solve(v, pl.mixed, v.vec_b, v.vec_x, s));
   L += 1;
   if (pl.mixed) {
     for (int it = 0; it < kRefineIters; ++it) {
-      RUN(launch_residual(v, s));
-      RUN(launch_solve(v, true, v.vec_r, v.vec_d, s));
-      RUN(launch_refine_update(v, s));
-      L += 3;
+      RUN(KC_REFINE, launch_residual(v, s));
+      RUN(KC_SOLVE, launch_solve(v, true, v.vec_r, v.vec_d, s));
+      RUN(KC_REFINE, launch_refine_update(v, s));
+      L += 5;
     }
-    RUN(launch_residual(v, s));
-    L += 1;
+    RUN(KC_REFINE, launch_residual(v, s));
+    L += 3;
   }
-  RUN(launch_lnl(v, s));
+  RUN(KC_LNL, launch_lnl(v, s));
   L += 1;
+  e = tick(-1);
+  if (e != cudaSuccess) return e;
 #undef RUN
   if (nlaunch) *nlaunch = L;
   return cudaSuccess;
@@ -540,13 +566,14 @@ int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, c
   if (!pl->exec) {
     // first use: run once directly (sets kernel attributes), then capture
     int64_t nl = 0;
-    CKC(c0, run_sequence(*pl, st, &nl));
+    CKC(c0, run_sequence(*pl, st, &nl, false));
     pl->launches = nl;
     CKC(c0, cudaStreamSynchronize(st));
     cudaStream_t cs;
     CKC(c0, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = run_sequence(*pl, cs, nullptr);
+    pl->prof = g_profiling;
+    if (e == cudaSuccess) e = run_sequence(*pl, cs, nullptr, pl->prof);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess) e = e2;
@@ -583,6 +610,21 @@ int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, c
     cudaGetLastError();
     ms = -1.0f;
   }
+  // per-class device time (profiled graphs only)
+  double cls_ms[kClasses] = {0};
+  int64_t cls_n[kClasses] = {0};
+  if (pl->prof && ms >= 0.0f) {
+    for (size_t i = 0; i + 1 < pl->pcls.size() + 1 && i + 1 < pl->pev.size(); ++i) {
+      if (i >= pl->pcls.size() || pl->pcls[i] < 0) break;
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, pl->pev[i], pl->pev[i + 1]) == cudaSuccess) {
+        cls_ms[pl->pcls[i]] += t;
+        cls_n[pl->pcls[i]] += 1;
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
   // diagnostics
   std::vector<double> resid(pl->P);
   CKC(c0, cudaMemcpy(resid.data(), pl->view.resid, sizeof(double) * pl->P, cudaMemcpyDeviceToHost));
@@ -594,6 +636,10 @@ int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, c
     double mx = 0.0;
     for (int b = 0; b < B[s]; ++b) mx = std::max(mx, resid[pl->first[s] + b]);
     c->stats.resid_rel_max = mx;
+    for (int q = 0; q < kClasses; ++q) {
+      c->stats.ms_class[q] = cls_ms[q];
+      c->stats.n_class[q] = cls_n[q];
+    }
     c->last_plan = pl;
     c->last_first = pl->first[s];
   }
@@ -666,6 +712,21 @@ int beor_get_dbar(beor_ctx* c, beor_c128* out) {
   cudaSetDevice(c->device);
   CKC(c, from_device(out, c->dbar.p, sizeof(double2) * c->n, 0));
   CKC(c, cudaDeviceSynchronize());
+  return BEOR_OK;
+}
+
+int beor_set_profiling(int on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_profiling = on != 0;
+  // graphs captured with the other setting are rebuilt on their next use
+  for (Plan* p : g_plans) {
+    if (p->prof != g_profiling && p->exec) {
+      cudaGraphExecDestroy(p->exec);
+      cudaGraphDestroy(p->graph);
+      p->exec = nullptr;
+      p->graph = nullptr;
+    }
+  }
   return BEOR_OK;
 }
 

@@ -194,8 +194,13 @@ def _cells(nu: int) -> np.ndarray:
     return np.array(out, dtype=np.int64)
 
 
-def build_instrument(spec: InstrumentSpec | str, with_data: bool = True) -> Instrument:
-    """Build the factored instrument (A_f, W), k-bin map, signal and data."""
+def build_instrument(spec: InstrumentSpec | str, with_data: bool = True,
+                     A_from: "Instrument | None" = None) -> Instrument:
+    """Build the factored instrument (A_f, W), k-bin map, signal and data.
+
+    A_from: an instrument with the same geometry, grid and channel plan but at
+    least as many channels; its per-frequency response matrices are reused
+    (sub-bands of one band share them)."""
     if isinstance(spec, str):
         spec = CONFIGS[spec]
     lat = math.radians(LATITUDE_DEG)
@@ -222,7 +227,14 @@ def build_instrument(spec: InstrumentSpec | str, with_data: bool = True) -> Inst
     BF = beam[:, None] * F_uv
     uv_m = _uv_at(bl, ha, lat).reshape(-1, 2)             # (n_tb, 2) metres, row = t*n_bl + b
     A = np.empty((spec.nf, spec.n_tb, spec.n_cells), dtype=np.complex128)
+    reuse = (A_from is not None and A_from.A.shape[0] >= spec.nf
+             and A_from.A.shape[1:] == A.shape[1:]
+             and np.allclose(A_from.freqs_hz[: spec.nf], freqs, rtol=0, atol=1e-6)
+             and abs(A_from.du - du) <= 1e-12 * du)
     for f, nu_f in enumerate(freqs):
+        if reuse:
+            A[f] = A_from.A[f]
+            continue
         uvw = uv_m * (nu_f / C_LIGHT)
         nudft = np.exp(-2j * np.pi * (np.outer(uvw[:, 0], l_flat) + np.outer(uvw[:, 1], m_flat)))
         A[f] = nudft @ BF

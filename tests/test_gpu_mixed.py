@@ -70,3 +70,23 @@ def test_mixed_matches_fp64_gpu_C0(P):
     la, _ = a.lnl(ph)
     lb, _ = b.lnl(ph)
     assert np.abs(la - lb).max() <= ATOL_LNL
+
+
+@pytest.mark.slow
+def test_mixed_and_fp64_C1_full_size(P):
+    """The 3280-mode instrument at full size: mixed |dlnL| <= 1e-2, abar rel
+    <= 1e-6; float64 GPU 1e-10 relative."""
+    ph = phis("C1", 2, stream=51)
+    refs = [oracle_eval("C1", p) for p in ph]
+    lm = make_like(P, "C1", precision="mixed")
+    got, st = lm.lnl(ph)
+    assert np.all(st == 0)
+    errs = np.abs(got - np.array([r["lnl"] for r in refs]))
+    print("C1 mixed |dlnL|", errs, lm.stats()["resid_rel_max"])
+    assert errs.max() <= ATOL_LNL
+    a, _ = lm.posterior_mean(ph[0])
+    assert np.linalg.norm(a - refs[0]["abar"]) <= RTOL_ABAR * np.linalg.norm(refs[0]["abar"])
+    lf = make_like(P, "C1", precision="fp64")
+    gf, sf = lf.lnl(ph)
+    assert np.all(sf == 0)
+    assert np.all(np.abs(gf - np.array([r["lnl"] for r in refs])) <= 1e-10 * np.abs([r["lnl"] for r in refs]))
