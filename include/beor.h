@@ -159,6 +159,25 @@ int beor_get_terms(const beor_ctx *ctx, double *logdet_phi, double *logdet_sigma
  * matrix by the factorisation (diagnostics and tests). */
 int beor_get_factor(const beor_ctx *ctx, int b, beor_c128 *L_out);
 
+/* dbar = T^H N^-1 d of a factored instrument (same arguments and result as
+ * the dbar of beor_set_instrument + beor_set_data + beor_precompute), for
+ * callers that cannot allocate device memory -- e.g. code running where
+ * another framework already owns all device memory in its own pool, or a
+ * loop that must never stall on cudaMalloc / cudaFree.  This call allocates
+ * nothing: the per-frequency partial sums live in a fixed 1 MiB device
+ * array built into the library, so it needs nf * ncells <= 65536 and
+ * returns BEOR_EINVAL beyond that.  All pointers must be device memory
+ * (BEOR_EINVAL otherwise): A nf x ntb x ncells, W nf x nx, noise_var and d
+ * nf*ntb, dbar_out ncells*nx.  The work is enqueued on `stream`; dbar_out
+ * is valid when the stream reaches it.  The first call on a device looks up
+ * the array's device address (make that first call before any stream
+ * capture).  Every call reuses the same array, so calls that may overlap on
+ * the GPU (different streams, or other host threads) race and must be
+ * serialised by the caller.  The paper has no counterpart of this call. */
+int beor_dbar_factored_noalloc(const beor_c128 *A, const beor_c128 *W, int nf, int64_t ntb,
+                               int ncells, int nx, const double *noise_var, const beor_c128 *d,
+                               beor_c128 *dbar_out, void *stream);
+
 /* ---------------------------------------------------------------------
  * Learned emulator of lnL(phi) (pre-screening for the nested sampler).
  * A multilayer perceptron n_in -> depth x width GELU -> 1 with bf16 weights
