@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SUBBANDS = ("C3_24", "C3_32", "C3_48")
+WORKLOADS = {"c3": SUBBANDS, "c1": ("C1",)}
 METRIC = "exact lnL evals/s at N_model~11k (C3 sub-band mix, mixed precision)"
 UNIT = "evals/s"
 # bf16 tensor operations of one trailing-update output tile (128 x 64 complex,
@@ -100,19 +101,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def build_workload(B: int):
+def build_workload(B: int, names=SUBBANDS):
     from synth import build_instrument, draw_phi
     insts = {}
-    insts["C3_48"] = build_instrument("C3_48")
-    for name in ("C3_24", "C3_32"):
-        insts[name] = build_instrument(name, A_from=insts["C3_48"])
-    phis = {n: draw_phi(insts[n].spec, B) for n in SUBBANDS}
+    if "C3_48" in names:
+        insts["C3_48"] = build_instrument("C3_48")
+        for name in ("C3_24", "C3_32"):
+            insts[name] = build_instrument(name, A_from=insts["C3_48"])
+    for name in names:
+        if name not in insts:
+            insts[name] = build_instrument(name)
+    phis = {n: draw_phi(insts[n].spec, B) for n in names}
     return insts, phis
 
 
-def make_likes(P, insts, precision):
+def make_likes(P, insts, precision, names=SUBBANDS):
     likes = []
-    for n in SUBBANDS:
+    for n in names:
         inst = insts[n]
         lk = P.Likelihood(precision)
         lk.set_instrument(inst.A, inst.W, inst.kbin, inst.spec.n_k, inst.spec.lssm_prior_var)
@@ -195,6 +200,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS),
+                    help="c3: the sub-band mix (default); c1: the 3280-mode instrument (small profiling case)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -208,16 +215,17 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     import paper_2501_12928_gb300 as P
 
-    insts, phis = build_workload(args.B)
-    n_models = [insts[n].spec.n_model for n in SUBBANDS]
+    names = WORKLOADS[args.workload]
+    insts, phis = build_workload(args.B, names)
+    n_models = [insts[n].spec.n_model for n in names]
     t0 = time.perf_counter()
-    likes = make_likes(P, insts, "mixed")
+    likes = make_likes(P, insts, "mixed", names)
     torch.cuda.synchronize()
     t_pre = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
-    dev_phi = [torch.tensor(phis[n], dtype=torch.float64, device="cuda") for n in SUBBANDS]
-    out = [torch.empty(args.B, dtype=torch.float64, device="cuda") for _ in SUBBANDS]
-    sts = [torch.empty(args.B, dtype=torch.int32, device="cuda") for _ in SUBBANDS]
+    dev_phi = [torch.tensor(phis[n], dtype=torch.float64, device="cuda") for n in names]
+    out = [torch.empty(args.B, dtype=torch.float64, device="cuda") for _ in names]
+    sts = [torch.empty(args.B, dtype=torch.int32, device="cuda") for _ in names]
     P.set_profiling(True)
 
     def step():
@@ -248,14 +256,14 @@ def main():
         t = torch.tensor([elapsed], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed = float(t.item())
-    evals_step = args.B * len(SUBBANDS)
+    evals_step = args.B * len(names)
     value = evals_step * args.steps * ws / elapsed
     launches = likes[0].stats()["kernel_launches"]
     status_ok = all(int((s != 0).sum().item()) == 0 for s in sts)
 
     # end to end through the public API with host buffers (copies inside the timed region)
     P.set_profiling(False)
-    host_phi = [np.ascontiguousarray(phis[n]) for n in SUBBANDS]
+    host_phi = [np.ascontiguousarray(phis[n]) for n in names]
     for _ in range(2):
         P.lnl_multi(likes, host_phi)
     torch.cuda.synchronize()
@@ -283,21 +291,21 @@ def main():
     fp64 = None
     if not args.no_fp64:
         P.set_profiling(False)
-        lf = make_likes(P, insts, "fp64")
-        ph1 = [phis[n][:1] for n in SUBBANDS]
+        lf = make_likes(P, insts, "fp64", names)
+        ph1 = [phis[n][:1] for n in names]
         P.lnl_multi(lf, ph1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.fp64_steps):
             P.lnl_multi(lf, ph1)
         dt = (time.perf_counter() - t0) / args.fp64_steps
-        fp64 = {"value": len(SUBBANDS) / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+        fp64 = {"value": len(names) / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
                 "workload": "one point per sub-band (N 6048/7840/11424) per batched evaluation"}
         for lk in lf:
             lk.close()
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and args.workload == "c3":
         cpu = cpu_baseline(insts, n_models)
 
     if rank == 0:
@@ -307,8 +315,10 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16 slice products (exact, fp32 accumulate) + double-float / f64",
             "data": "synthetic",
-            "config": {"workload": "C3: 3 sub-band instruments (n_f 24/32/48, N_model 6048/7840/11424, "
-                                   "331 baselines x 16 times), B=16 each, one batched evaluation per step",
+            "config": {"workload": ("C3: 3 sub-band instruments (n_f 24/32/48, N_model 6048/7840/11424, "
+                                    "331 baselines x 16 times), B=%d each, one batched evaluation per step" % args.B)
+                       if args.workload == "c3" else
+                       "C1: one instrument (N_model 3280, 126 baselines x 19 times x 38 channels), B=%d" % args.B,
                        "B_per_subband": args.B, "n_model": n_models, "precompute_s": round(t_pre, 2),
                        "l2": "inputs larger than L2 (working matrices ~30 GB)", "parallelism": "replicas"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * sum(p.size for p in host_phi),

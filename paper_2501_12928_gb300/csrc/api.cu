@@ -195,13 +195,13 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
     }
   }
   RUN(KC_SOLVE, launch_solve(v, pl.mixed, v.vec_b, v.vec_x, s));
-  L += 1;
+  L += solve_launch_count(pl.max_nt);
   if (pl.mixed) {
     for (int it = 0; it < kRefineIters; ++it) {
       RUN(KC_REFINE, launch_residual(v, s));
       RUN(KC_SOLVE, launch_solve(v, true, v.vec_r, v.vec_d, s));
       RUN(KC_REFINE, launch_refine_update(v, s));
-      L += 5;
+      L += 4 + solve_launch_count(pl.max_nt);
     }
     RUN(KC_REFINE, launch_residual(v, s));
     L += 3;

@@ -54,6 +54,7 @@ cudaError_t launch_diag(const BatchView& v, int k, bool mixed, cudaStream_t s);
 cudaError_t launch_panel_f64(const BatchView& v, int k, cudaStream_t s);
 cudaError_t launch_trail_f64(const BatchView& v, int k, cudaStream_t s);
 cudaError_t launch_solve(const BatchView& v, bool mixed, const double2* rhs, double2* out, cudaStream_t s);
+int solve_launch_count(int max_nt);
 cudaError_t launch_lnl(const BatchView& v, cudaStream_t s);
 cudaError_t launch_copy_dbar(const BatchView& v, cudaStream_t s);
 

@@ -418,108 +418,222 @@ cudaError_t launch_trail_f64(const BatchView& v, int k, cudaStream_t s) {
 }
 
 // --------------------------------------------------------------------------
-// Triangular solves with the factor: out = L^-H L^-1 rhs.  One CTA per
-// problem; diagonal blocks through the float64 inverse, off-diagonal tiles
-// in float64 (both element types are read as float64).
+// Triangular solves with the factor: out = L^-H L^-1 rhs, blocked by 128.
+// One launch per block step covers every problem: CTA (i, p) applies the
+// update of block row i with the block just solved; the CTA that completes
+// the next block row also applies that block's float64 inverse, so a step's
+// critical path is one tile update plus one 128 x 128 float64 matvec.
+// Off-diagonal products: float64 for the float64 path, double-float (fp32
+// pairs) for the mixed path's double-float factor.
 // --------------------------------------------------------------------------
+struct CAcc {          // complex accumulator
+  double2 d;           // float64 path
+  dfl re, im;          // double-float path
+};
+
+__device__ __forceinline__ void cacc_zero(CAcc& a) {
+  a.d = make_double2(0.0, 0.0);
+  a.re = dfl{0.0f, 0.0f};
+  a.im = dfl{0.0f, 0.0f};
+}
+// a += L * y (conj_l: a += conj(L) * y); y given as double2 and as double-float pairs
+__device__ __forceinline__ void cacc_mac(CAcc& a, const double2* L, double2 y, dfl, dfl, bool conj_l) {
+  const double2 l = *L;
+  const double li = conj_l ? -l.y : l.y;
+  a.d.x = fma(l.x, y.x, fma(-li, y.y, a.d.x));
+  a.d.y = fma(l.x, y.y, fma(li, y.x, a.d.y));
+}
+__device__ __forceinline__ void cacc_mac(CAcc& a, const float4* L, double2, dfl yr, dfl yi, bool conj_l) {
+  const float4 l = *L;
+  const dfl lr{l.x, l.y};
+  const dfl li = conj_l ? dfl{-l.z, -l.w} : dfl{l.z, l.w};
+  a.re = df_add(a.re, df_add(df_mul(lr, yr), df_neg(df_mul(li, yi))));
+  a.im = df_add(a.im, df_add(df_mul(lr, yi), df_mul(li, yr)));
+}
+__device__ __forceinline__ double2 cacc_get(const CAcc& a, const double2*) { return a.d; }
+__device__ __forceinline__ double2 cacc_get(const CAcc& a, const float4*) {
+  return make_double2(df_to_double(a.re), df_to_double(a.im));
+}
+__device__ __forceinline__ void cacc_add(CAcc& a, const CAcc& b) {
+  a.d.x += b.d.x;
+  a.d.y += b.d.y;
+  a.re = df_add(a.re, b.re);
+  a.im = df_add(a.im, b.im);
+}
+__device__ __forceinline__ CAcc cacc_shfl_xor(const CAcc& a, int o) {
+  CAcc b;
+  b.d.x = __shfl_xor_sync(0xffffffffu, a.d.x, o);
+  b.d.y = __shfl_xor_sync(0xffffffffu, a.d.y, o);
+  b.re.hi = __shfl_xor_sync(0xffffffffu, a.re.hi, o);
+  b.re.lo = __shfl_xor_sync(0xffffffffu, a.re.lo, o);
+  b.im.hi = __shfl_xor_sync(0xffffffffu, a.im.hi, o);
+  b.im.lo = __shfl_xor_sync(0xffffffffu, a.im.lo, o);
+  return b;
+}
+
+// y_blk = Linv (or Linv^H when herm) * r_blk, float64; 128 threads of the CTA
+__device__ __forceinline__ void diag_apply(const double2* __restrict__ li, const double2* rk, double2* out,
+                                           bool herm) {
+  const int t = threadIdx.x;
+  if (t >= BEOR_TB) return;
+  double sr = 0.0, si = 0.0;
+  if (!herm) {
+    for (int m = 0; m <= t; ++m) {
+      const double2 a = li[pk(t, m)], q = rk[m];
+      sr = fma(a.x, q.x, fma(-a.y, q.y, sr));
+      si = fma(a.x, q.y, fma(a.y, q.x, si));
+    }
+  } else {
+    for (int m = t; m < BEOR_TB; ++m) {
+      const double2 a = li[pk(m, t)], q = rk[m];
+      sr = fma(a.x, q.x, fma(a.y, q.y, sr));
+      si = fma(a.x, q.y, fma(-a.y, q.x, si));
+    }
+  }
+  out[t] = make_double2(sr, si);
+}
+
+// Forward step k (k = -1: only y_0).  CTA (i, p), i = k+1 .. nt-1:
+// r_i -= L_ik y_k; the CTA with i == k+1 then sets y_{k+1} = Linv r_{k+1}.
 template <typename WS>
-__global__ void __launch_bounds__(256) solve_kernel(BatchView v, const double2* __restrict__ rhs,
-                                                    double2* __restrict__ out) {
-  __shared__ double2 rk[BEOR_TB];
+__global__ void __launch_bounds__(256) fwd_step_kernel(BatchView v, int k, const double2* __restrict__ rhs) {
   __shared__ double2 yk[BEOR_TB];
-  const int p = blockIdx.x;
+  __shared__ dfl ykr[BEOR_TB], yki[BEOR_TB];
+  __shared__ CAcc part[BEOR_TB];
+  __shared__ double2 rk[BEOR_TB];
+  const int p = blockIdx.y;
   const Prob pr = v.prob[p];
-  if (v.status[p] > 0) return;
-  const int np = pr.nt * BEOR_TB;
-  const WS* ws = reinterpret_cast<const WS*>(v.ws) + pr.ws_off;
+  const int i = k + 1 + blockIdx.x;
+  if (i >= pr.nt || v.status[p] > 0) return;
+  const int tid = threadIdx.x;
   double2* r = v.vec_t + pr.row_off;
   double2* y = v.vec_y + pr.row_off;
-  double2* x = out + pr.row_off;
-  const double2* b = rhs + pr.row_off;
+  if (k < 0) {
+    // initial step: r = rhs for all rows of block 0 handled here, other rows by their own CTAs
+    if (tid < BEOR_TB) r[i * BEOR_TB + tid] = rhs[pr.row_off + i * BEOR_TB + tid];
+    if (i != 0) return;
+    __syncthreads();
+    if (tid < BEOR_TB) rk[tid] = r[tid];
+    __syncthreads();
+    diag_apply(v.dinv + pr.dinv_off, rk, yk, false);
+    __syncthreads();
+    if (tid < BEOR_TB) y[tid] = yk[tid];
+    return;
+  }
+  if (tid < BEOR_TB) {
+    const double2 q = y[k * BEOR_TB + tid];
+    yk[tid] = q;
+    ykr[tid] = df_from_double(q.x);
+    yki[tid] = df_from_double(q.y);
+  }
+  __syncthreads();
+  const WS* t = reinterpret_cast<const WS*>(v.ws) + pr.ws_off + tri_index(i, k) * BEOR_TILE_ELEMS;
+  const int row = tid & 127, half = tid >> 7;
+  CAcc a;
+  cacc_zero(a);
+#pragma unroll 4
+  for (int m = half * 64; m < half * 64 + 64; ++m)
+    cacc_mac(a, t + m * BEOR_TB + row, yk[m], ykr[m], yki[m], false);
+  if (half) part[row] = a;
+  __syncthreads();
+  if (!half) {
+    cacc_add(a, part[row]);
+    const double2 s = cacc_get(a, t);
+    double2 cur = r[i * BEOR_TB + row];
+    cur.x -= s.x;
+    cur.y -= s.y;
+    r[i * BEOR_TB + row] = cur;
+    rk[row] = cur;
+  }
+  if (i != k + 1) return;
+  __syncthreads();
+  diag_apply(v.dinv + pr.dinv_off + (int64_t)i * DG_PACK, rk, yk, false);
+  __syncthreads();
+  if (tid < BEOR_TB) y[i * BEOR_TB + tid] = yk[tid];
+}
+
+// Backward step k (k = nt: only x_{nt-1} for each problem).  CTA (i, p),
+// i = 0 .. k-1: r_i -= L_ki^H x_k; the CTA with i == k-1 then sets
+// x_{k-1} = Linv^H r_{k-1}.  Steps run from the largest nt down; problems
+// with fewer tiles join when k < their nt.
+template <typename WS>
+__global__ void __launch_bounds__(256) bwd_step_kernel(BatchView v, int k, double2* __restrict__ out) {
+  __shared__ double2 xk[BEOR_TB];
+  __shared__ dfl xkr[BEOR_TB], xki[BEOR_TB];
+  __shared__ double2 rk[BEOR_TB];
+  const int p = blockIdx.y;
+  const Prob pr = v.prob[p];
+  if (v.status[p] > 0) return;
   const int tid = threadIdx.x;
-  for (int j = tid; j < np; j += blockDim.x) r[j] = b[j];
-  __syncthreads();
-  // forward: L y = b
-  for (int k = 0; k < pr.nt; ++k) {
-    if (tid < BEOR_TB) rk[tid] = r[k * BEOR_TB + tid];
+  double2* r = v.vec_t + pr.row_off;
+  double2* x = out + pr.row_off;
+  const double2* y = v.vec_y + pr.row_off;
+  if (k >= pr.nt) {
+    // start: r = y; the CTA for the last block applies Linv^H
+    const int i = blockIdx.x;
+    if (i >= pr.nt) return;
+    if (tid < BEOR_TB) r[i * BEOR_TB + tid] = y[i * BEOR_TB + tid];
+    if (k != pr.nt || i != pr.nt - 1) return;
     __syncthreads();
-    const double2* li = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
-    if (tid < BEOR_TB) {
-      double sr = 0.0, si = 0.0;
-      for (int m = 0; m <= tid; ++m) {
-        double2 a = li[pk(tid, m)], q = rk[m];
-        sr = fma(a.x, q.x, fma(-a.y, q.y, sr));
-        si = fma(a.x, q.y, fma(a.y, q.x, si));
-      }
-      yk[tid] = make_double2(sr, si);
-      y[k * BEOR_TB + tid] = yk[tid];
-    }
+    if (tid < BEOR_TB) rk[tid] = r[i * BEOR_TB + tid];
     __syncthreads();
-    for (int i = k + 1 + (tid >> 7); i < pr.nt; i += 2) {
-      const int row = tid & 127;
-      const WS* t = ws + tri_index(i, k) * BEOR_TILE_ELEMS;
-      double sr = 0.0, si = 0.0;
-      for (int m = 0; m < BEOR_TB; ++m) {
-        double2 a = ws_load(t + m * BEOR_TB + row), q = yk[m];
-        sr = fma(a.x, q.x, fma(-a.y, q.y, sr));
-        si = fma(a.x, q.y, fma(a.y, q.x, si));
-      }
-      double2 cur = r[i * BEOR_TB + row];
-      r[i * BEOR_TB + row] = make_double2(cur.x - sr, cur.y - si);
-    }
+    diag_apply(v.dinv + pr.dinv_off + (int64_t)i * DG_PACK, rk, xk, true);
     __syncthreads();
+    if (tid < BEOR_TB) x[i * BEOR_TB + tid] = xk[tid];
+    return;
   }
-  // backward: L^H x = y
-  for (int j = tid; j < np; j += blockDim.x) r[j] = y[j];
+  const int i = blockIdx.x;
+  if (i >= k) return;
+  if (tid < BEOR_TB) {
+    const double2 q = x[k * BEOR_TB + tid];
+    xk[tid] = q;
+    xkr[tid] = df_from_double(q.x);
+    xki[tid] = df_from_double(q.y);
+  }
   __syncthreads();
+  const WS* t = reinterpret_cast<const WS*>(v.ws) + pr.ws_off + tri_index(k, i) * BEOR_TILE_ELEMS;
   const int warp = tid >> 5, lane = tid & 31;
-  for (int k = pr.nt - 1; k >= 0; --k) {
-    if (tid < BEOR_TB) rk[tid] = r[k * BEOR_TB + tid];
-    __syncthreads();
-    const double2* li = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
-    if (tid < BEOR_TB) {
-      double sr = 0.0, si = 0.0;
-      for (int m = tid; m < BEOR_TB; ++m) {
-        double2 a = li[pk(m, tid)], q = rk[m];
-        // conj(a) * q
-        sr = fma(a.x, q.x, fma(a.y, q.y, sr));
-        si = fma(a.x, q.y, fma(-a.y, q.x, si));
-      }
-      yk[tid] = make_double2(sr, si);
-      x[k * BEOR_TB + tid] = yk[tid];
+  for (int c = warp; c < BEOR_TB; c += 8) {
+    CAcc a;
+    cacc_zero(a);
+#pragma unroll
+    for (int m = lane; m < BEOR_TB; m += 32) cacc_mac(a, t + c * BEOR_TB + m, xk[m], xkr[m], xki[m], true);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cacc_add(a, cacc_shfl_xor(a, o));
+    if (lane == 0) {
+      const double2 s = cacc_get(a, t);
+      double2 cur = r[i * BEOR_TB + c];
+      cur.x -= s.x;
+      cur.y -= s.y;
+      r[i * BEOR_TB + c] = cur;
+      rk[c] = cur;
     }
-    __syncthreads();
-    // r_i -= L_ki^H x_k for i < k: one warp per column c' of tile (k, i)
-    for (int i = 0; i < k; ++i) {
-      const WS* t = ws + tri_index(k, i) * BEOR_TILE_ELEMS;
-      for (int c = warp; c < BEOR_TB; c += (int)(blockDim.x >> 5)) {
-        double sr = 0.0, si = 0.0;
-        for (int m = lane; m < BEOR_TB; m += 32) {
-          double2 a = ws_load(t + c * BEOR_TB + m), q = yk[m];
-          sr = fma(a.x, q.x, fma(a.y, q.y, sr));
-          si = fma(a.x, q.y, fma(-a.y, q.x, si));
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          sr += __shfl_xor_sync(0xffffffffu, sr, o);
-          si += __shfl_xor_sync(0xffffffffu, si, o);
-        }
-        if (lane == 0) {
-          double2 cur = r[i * BEOR_TB + c];
-          r[i * BEOR_TB + c] = make_double2(cur.x - sr, cur.y - si);
-        }
-      }
-    }
-    __syncthreads();
   }
+  if (i != k - 1) return;
+  __syncthreads();
+  diag_apply(v.dinv + pr.dinv_off + (int64_t)i * DG_PACK, rk, xk, true);
+  __syncthreads();
+  if (tid < BEOR_TB) x[i * BEOR_TB + tid] = xk[tid];
+}
+
+template <typename WS>
+static cudaError_t solve_impl(const BatchView& v, const double2* rhs, double2* out, cudaStream_t s) {
+  const int nt = v.max_nt;
+  fwd_step_kernel<WS><<<dim3(nt, v.P), 256, 0, s>>>(v, -1, rhs);
+  for (int k = 0; k + 1 < nt; ++k) fwd_step_kernel<WS><<<dim3(nt - k - 1, v.P), 256, 0, s>>>(v, k, rhs);
+  bwd_step_kernel<WS><<<dim3(nt, v.P), 256, 0, s>>>(v, nt, out);
+  for (int k = nt - 1; k >= 1; --k) {
+    // problems whose last block is k-1 (nt_p == k) start here
+    bwd_step_kernel<WS><<<dim3(k, v.P), 256, 0, s>>>(v, k, out);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_solve(const BatchView& v, bool mixed, const double2* rhs, double2* out, cudaStream_t s) {
-  if (mixed)
-    solve_kernel<float4><<<v.P, 256, 0, s>>>(v, rhs, out);
-  else
-    solve_kernel<double2><<<v.P, 256, 0, s>>>(v, rhs, out);
-  return cudaGetLastError();
+  return mixed ? solve_impl<float4>(v, rhs, out, s) : solve_impl<double2>(v, rhs, out, s);
 }
+
+int solve_launch_count(int max_nt) { return 2 * max_nt; }
 
 // --------------------------------------------------------------------------
 // dbar of each problem's set into the right-hand-side vector
