@@ -41,7 +41,7 @@ struct BatchView {
   double* resid;             // [P] refinement residual norm ratio
   Flags* flags;
   // mixed path slice buffers
-  __nv_bfloat16* panel_sl;   // [NPLANE][rows][128]
+  __nv_bfloat16* panel_sl;   // [NPLANE][rows][128], plane = part * NSLICE + slice (part 0 re, 1 im)
   int32_t* panel_exp;        // [rows]
   __nv_bfloat16* linv_sl;    // [NPLANE][P*128][128]
   int32_t* linv_exp;         // [P*128]

@@ -131,19 +131,20 @@ __device__ __forceinline__ int row_exponent(double mx) {
   if (!(mx > 0.0)) return -1000;
   return ilogb(mx) + 1;
 }
+// Balanced base-256 digits of the 64-bit fixed-point number round(x * 2^(39 - e)):
+// one float64 scaling and conversion, then integer arithmetic.
 __device__ __forceinline__ void slice_value(double x, int e, __nv_bfloat16* out, int64_t plane_stride) {
-  if (e <= -1000) {
+  long long X = e <= -1000 ? 0 : llrint(ldexp(x, 39 - e));
+  int dg[BEOR_NSLICE];
 #pragma unroll
-    for (int s = 0; s < BEOR_NSLICE; ++s) out[s * plane_stride] = __float2bfloat16_rn(0.0f);
-    return;
+  for (int s = BEOR_NSLICE - 1; s >= 1; --s) {
+    const long long m = ((X + 128) & 255) - 128;
+    dg[s] = (int)m;
+    X = (X - m) >> 8;
   }
-  double y = ldexp(x, 7 - e);
+  dg[0] = (int)X;
 #pragma unroll
-  for (int s = 0; s < BEOR_NSLICE; ++s) {
-    double q = rint(y);
-    y = (y - q) * 256.0;
-    out[s * plane_stride] = __float2bfloat16_rn((float)ldexp(q, -8 * s));
-  }
+  for (int s = 0; s < BEOR_NSLICE; ++s) out[s * plane_stride] = __float2bfloat16_rn(ldexpf((float)dg[s], -8 * s));
 }
 
 // --------------------------------------------------------------------------
@@ -224,13 +225,23 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
     double2 t = make_double2(0.0, 0.0);
     if (tid < i) {
       const int j = tid;
-      double sr = 0.0, si = 0.0;
-      for (int m = j; m < i; ++m) {
-        double2 a = A[pk(i, m)], b = A[pk(m, j)];
-        sr = fma(a.x, b.x, fma(-a.y, b.y, sr));
-        si = fma(a.x, b.y, fma(a.y, b.x, si));
+      double sr0 = 0.0, si0 = 0.0, sr1 = 0.0, si1 = 0.0;   // two chains each
+      int m = j;
+      for (; m + 1 < i; m += 2) {
+        const double2 a = A[pk(i, m)], b = A[pk(m, j)];
+        const double2 c = A[pk(i, m + 1)], d = A[pk(m + 1, j)];
+        sr0 = fma(a.x, b.x, fma(-a.y, b.y, sr0));
+        si0 = fma(a.x, b.y, fma(a.y, b.x, si0));
+        sr1 = fma(c.x, d.x, fma(-c.y, d.y, sr1));
+        si1 = fma(c.x, d.y, fma(c.y, d.x, si1));
       }
-      t = make_double2(-sr / lii, -si / lii);
+      if (m < i) {
+        const double2 a = A[pk(i, m)], b = A[pk(m, j)];
+        sr0 = fma(a.x, b.x, fma(-a.y, b.y, sr0));
+        si0 = fma(a.x, b.y, fma(a.y, b.x, si0));
+      }
+      const double inv = 1.0 / lii;
+      t = make_double2(-(sr0 + sr1) * inv, -(si0 + si1) * inv);
     }
     __syncthreads();
     if (tid < i) A[pk(i, tid)] = t;
@@ -252,11 +263,11 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
       const int64_t row = (int64_t)p * BEOR_TB + c;
       const int64_t lrows = (int64_t)v.P * BEOR_TB;
       v.linv_exp[row] = e;
-      const int64_t ps = 2 * lrows * BEOR_TB;   // stride between slices (two planes each)
+      const int64_t ps = lrows * BEOR_TB;   // planes [part][slice]: slice stride is one plane
       for (int m = 0; m < BEOR_TB; ++m) {
         double2 a = m <= c ? A[pk(c, m)] : make_double2(0.0, 0.0);
-        slice_value(a.x, e, v.linv_sl + (0 * lrows + row) * BEOR_TB + m, ps);
-        slice_value(a.y, e, v.linv_sl + (1 * lrows + row) * BEOR_TB + m, ps);
+        slice_value(a.x, e, v.linv_sl + (0 * BEOR_NSLICE * lrows + row) * BEOR_TB + m, ps);
+        slice_value(a.y, e, v.linv_sl + (1 * BEOR_NSLICE * lrows + row) * BEOR_TB + m, ps);
       }
     }
   }

@@ -147,6 +147,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major operand, 32-byte swizzle, 8-row
@@ -161,9 +169,9 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
   d |= (uint64_t)6 << 61;                               // swizzle mode: 32 B
   return d;
 }
-// Instruction descriptor: bf16 x bf16 -> fp32, K-major A and B, M = 128, N = 64.
-__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t negate_a) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (negate_a << 13) | ((uint32_t)(MX_N >> 3) << 17) |
+// Instruction descriptor: bf16 x bf16 -> fp32, K-major A and B, M = 128, N given.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t negate_a, uint32_t n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (negate_a << 13) | ((n >> 3) << 17) |
          ((uint32_t)(MX_M >> 4) << 24);
 }
 
@@ -283,7 +291,6 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       uint32_t it = 0, tcount = 0;
-      constexpr uint32_t ID_POS = idesc_bf16(0), ID_NEG = idesc_bf16(1);
       for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         TileJob jb = decode_tile(v, prefix, t, k, MODE);
         if (!jb.valid) continue;
@@ -305,25 +312,35 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           }
           tc_fence_after();
           const uint32_t a0 = sbase + s * MX_STAGE_BYTES, b0 = a0 + MX_A_BYTES;
-          // plane p = slice*2 + part (0 re, 1 im)
+          // Planes are stored [part][slice] (part 0 re, 1 im), so the B slices
+          // t = 0..3-sa are contiguous rows: one MMA with N = 64 (4 - sa)
+          // writes the level accumulators sa..3 at once (TMEM columns: re
+          // levels 0..3 in [0, 256), im levels in [256, 512)); the pair
+          // t = 4 - sa adds into level 3 with N = 64.
 #pragma unroll
           for (int sa = 0; sa < BEOR_NSLICE; ++sa) {
-#pragma unroll
-            for (int sb = 0; sb < BEOR_NSLICE - sa; ++sb) {
-              const int lvl = (sa + sb) < 3 ? (sa + sb) : 3;
-              const uint32_t d_re = tmem + (uint32_t)(lvl * 2 + 0) * MX_N;
-              const uint32_t d_im = tmem + (uint32_t)(lvl * 2 + 1) * MX_N;
-              // first contribution to each accumulator of a tile overwrites it
-              // (loop order: the first pair of every level has sa == 0)
-              const uint32_t acc0 = (kc == 0 && sa == 0 && sb <= 3) ? 0u : 1u;
-              const uint64_t ar = sdesc_sw32(a0 + (sa * 2 + 0) * (MX_M * 32));
-              const uint64_t ai = sdesc_sw32(a0 + (sa * 2 + 1) * (MX_M * 32));
-              const uint64_t br = sdesc_sw32(b0 + (sb * 2 + 0) * (MX_N * 32));
-              const uint64_t bi = sdesc_sw32(b0 + (sb * 2 + 1) * (MX_N * 32));
-              tc_mma(d_re, ar, br, ID_POS, acc0);
-              tc_mma(d_re, ai, bi, ID_POS, 1u);
-              tc_mma(d_im, ai, br, ID_POS, acc0);
-              tc_mma(d_im, ar, bi, ID_NEG, 1u);
+            const uint64_t ar = sdesc_sw32(a0 + (0 * BEOR_NSLICE + sa) * (MX_M * 32));
+            const uint64_t ai = sdesc_sw32(a0 + (1 * BEOR_NSLICE + sa) * (MX_M * 32));
+            const uint32_t acc0 = (kc == 0 && sa == 0) ? 0u : 1u;
+            if (sa <= 3) {
+              const uint32_t n = (uint32_t)MX_N * (4 - sa);
+              const uint64_t br = sdesc_sw32(b0 + (0 * BEOR_NSLICE + 0) * (MX_N * 32));
+              const uint64_t bi = sdesc_sw32(b0 + (1 * BEOR_NSLICE + 0) * (MX_N * 32));
+              const uint32_t d_re = tmem + (uint32_t)(sa * MX_N), d_im = tmem + 256u + (uint32_t)(sa * MX_N);
+              tc_mma(d_re, ar, br, idesc_bf16(0, n), acc0);
+              tc_mma(d_re, ai, bi, idesc_bf16(0, n), 1u);
+              tc_mma(d_im, ai, br, idesc_bf16(0, n), acc0);
+              tc_mma(d_im, ar, bi, idesc_bf16(1, n), 1u);
+            }
+            {
+              const int tb = 4 - sa;
+              const uint64_t br = sdesc_sw32(b0 + (0 * BEOR_NSLICE + tb) * (MX_N * 32));
+              const uint64_t bi = sdesc_sw32(b0 + (1 * BEOR_NSLICE + tb) * (MX_N * 32));
+              const uint32_t d_re = tmem + 3u * MX_N, d_im = tmem + 256u + 3u * MX_N;
+              tc_mma(d_re, ar, br, idesc_bf16(0, MX_N), 1u);
+              tc_mma(d_re, ai, bi, idesc_bf16(0, MX_N), 1u);
+              tc_mma(d_im, ai, br, idesc_bf16(0, MX_N), 1u);
+              tc_mma(d_im, ar, bi, idesc_bf16(1, MX_N), 1u);
             }
           }
           tc_commit(empty_bar(s));
@@ -355,43 +372,54 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       const int32_t* ecol = MODE == MODE_TRAIL ? v.panel_exp + pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N
                                                : v.linv_exp + (int64_t)jb.p * BEOR_TB + jb.h * MX_N;
       const int out_j = MODE == MODE_TRAIL ? jb.j : k;
-      float4* C = reinterpret_cast<float4*>(v.ws) + pr.ws_off + tri_index(jb.i, out_j) * BEOR_TILE_ELEMS +
+      float4* __restrict__ C = reinterpret_cast<float4*>(v.ws) + pr.ws_off + tri_index(jb.i, out_j) * BEOR_TILE_ELEMS +
                   (int64_t)(jb.h * MX_N) * BEOR_TB + r;
       const uint32_t trow = tmem + ((uint32_t)lane_base << 16);
+      constexpr int EC = 8;   // columns per epilogue chunk
+      float4 cv[EC], cn[EC];
+      if (MODE == MODE_TRAIL) {
+#pragma unroll
+        for (int q = 0; q < EC; ++q) cv[q] = __ldcs(C + (int64_t)q * BEOR_TB);
+      }
 #pragma unroll 1
-      for (int c0 = 0; c0 < MX_N; c0 += 16) {
-        float a0r[16], a0i[16], a1r[16], a1i[16], a2r[16], a2i[16], a3r[16], a3i[16];
-        tmem_ld16(trow + 0 * MX_N + c0, a0r);
-        tmem_ld16(trow + 1 * MX_N + c0, a0i);
-        tmem_ld16(trow + 2 * MX_N + c0, a1r);
-        tmem_ld16(trow + 3 * MX_N + c0, a1i);
-        tmem_ld16(trow + 4 * MX_N + c0, a2r);
-        tmem_ld16(trow + 5 * MX_N + c0, a2i);
-        tmem_ld16(trow + 6 * MX_N + c0, a3r);
-        tmem_ld16(trow + 7 * MX_N + c0, a3i);
+      for (int c0 = 0; c0 < MX_N; c0 += EC) {
+        // prefetch the next chunk of the working matrix while this one is processed
+        if (MODE == MODE_TRAIL && c0 + EC < MX_N) {
+#pragma unroll
+          for (int q = 0; q < EC; ++q) cn[q] = __ldcs(C + (int64_t)(c0 + EC + q) * BEOR_TB);
+        }
+        float lr[4][EC], li[4][EC];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          tmem_ld8(trow + (uint32_t)(l * MX_N + c0), lr[l]);
+          tmem_ld8(trow + 256u + (uint32_t)(l * MX_N + c0), li[l]);
+        }
         tmem_ld_wait();
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int c = c0 + q;
-          const int ec = __ldg(ecol + c);
+        for (int q = 0; q < EC; ++q) {
+          const int ec = __ldg(ecol + c0 + q);
           int ex = e_r + ec - 14;
           if (e_r <= -1000 || ec <= -1000) ex = 0;
           ex = max(-250, min(250, ex));
           const int e1 = ex >> 1, e2 = ex - e1;   // two exact power-of-two factors
           const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
-          dfl vr = df_add(df_two_sum(a0r[q], a1r[q]), df_two_sum(a2r[q], a3r[q]));
-          dfl vi = df_add(df_two_sum(a0i[q], a1i[q]), df_two_sum(a2i[q], a3i[q]));
+          dfl vr = df_add(df_two_sum(lr[0][q], lr[1][q]), df_two_sum(lr[2][q], lr[3][q]));
+          dfl vi = df_add(df_two_sum(li[0][q], li[1][q]), df_two_sum(li[2][q], li[3][q]));
           vr.hi = vr.hi * s1 * s2; vr.lo = vr.lo * s1 * s2;
           vi.hi = vi.hi * s1 * s2; vi.lo = vi.lo * s1 * s2;
-          float4* cp = C + (int64_t)c * BEOR_TB;
+          float4* cp = C + (int64_t)(c0 + q) * BEOR_TB;
           if (MODE == MODE_TRAIL) {
-            float4 w = *cp;
-            dfl wr = df_add(dfl{w.x, w.y}, df_neg(vr));
-            dfl wi = df_add(dfl{w.z, w.w}, df_neg(vi));
-            *cp = make_float4(wr.hi, wr.lo, wi.hi, wi.lo);
+            const float4 w = cv[q];
+            const dfl wr = df_add(dfl{w.x, w.y}, df_neg(vr));
+            const dfl wi = df_add(dfl{w.z, w.w}, df_neg(vi));
+            __stcs(cp, make_float4(wr.hi, wr.lo, wi.hi, wi.lo));
           } else {
-            *cp = make_float4(vr.hi, vr.lo, vi.hi, vi.lo);
+            __stcs(cp, make_float4(vr.hi, vr.lo, vi.hi, vi.lo));
           }
+        }
+        if (MODE == MODE_TRAIL) {
+#pragma unroll
+          for (int q = 0; q < EC; ++q) cv[q] = cn[q];
         }
       }
       tc_fence_before();
@@ -456,7 +484,7 @@ __global__ void __launch_bounds__(256) slice_panel_kernel(BatchView v, int k) {
         dg[0] = (int)X;
 #pragma unroll
         for (int sl = 0; sl < BEOR_NSLICE; ++sl) {
-          __nv_bfloat16* dst = v.panel_sl + ((int64_t)(sl * 2 + part) * rows + grow) * BEOR_TB + lane + 32 * q;
+          __nv_bfloat16* dst = v.panel_sl + ((int64_t)(part * BEOR_NSLICE + sl) * rows + grow) * BEOR_TB + lane + 32 * q;
           *dst = __float2bfloat16_rn(ldexpf((float)dg[sl], -8 * sl));
         }
       }
