@@ -121,7 +121,8 @@ class NestedSampler:
         empty = 0
         while len(acc_x) < need:
             cand = self._draw_block(mu, chol, self.batch)
-            if self.screen is not None and lmin < self.screen_limit and empty < self.max_empty_blocks:
+            limit = getattr(getattr(self, "_screen_owner", None), "support_limit", self.screen_limit)
+            if self.screen is not None and lmin < limit and empty < self.max_empty_blocks:
                 pred = np.asarray(self.screen(cand), float)
                 keep = pred >= lmin - self.delta
                 self.n_screened += int((~keep).sum())

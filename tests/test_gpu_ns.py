@@ -24,3 +24,20 @@ def test_emulator_screen_saves_exact_evaluations():
     print(out)
     assert abs(out["dlogz"]) <= 0.1
     assert out["emulator"]["n_exact"] < out["exact"]["n_exact"]
+
+
+def test_active_emulator_screen():
+    """Refitting the emulator on the sampler's own exact evaluations extends
+    the screen's support up the likelihood; ln Z still matches the exact run."""
+    import paper_2501_12928_gb300 as P
+    from paper_2501_12928_gb300.emulated_sampler import ExactLikelihood, compare_runs_active, make_training_set
+    from tests.gpu_common import make_like
+
+    lk = make_like(P, "C0", precision="mixed")
+    exact = ExactLikelihood(lk, max_batch=256)
+    phi, lnl = make_training_set(exact, 4, 8192, seed=17)
+    out = compare_runs_active(exact, phi, lnl, 4, n_live=100, k_remove=8, batch=64, seed=5, every=10,
+                              width=128, depth=3, epochs=30, train_batch=512)
+    print(out)
+    assert abs(out["dlogz"]) <= 0.1
+    assert out["emulator"]["n_exact"] < out["exact"]["n_exact"]
