@@ -253,9 +253,8 @@ def main():
         torch.cuda.synchronize()
     elapsed = e0.elapsed_time(e1) / 1e3
     if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        from paper_2501_12928_gb300.replicas import max_over_ranks
+        elapsed = max_over_ranks(elapsed)
     evals_step = args.B * len(names)
     value = evals_step * args.steps * ws / elapsed
     launches = likes[0].stats()["kernel_launches"]
