@@ -171,17 +171,14 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
   }
   if (tid == 0) s_fail = 0;
   __syncthreads();
-  double ld = 0.0;   // thread 0 accumulates
   const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
   for (int j = 0; j < BEOR_TB; ++j) {
     if (tid == 0) {
-      double d = A[pk(j, j)].x;
+      const double d = A[pk(j, j)].x;
       if (!(d > 0.0) || !isfinite(d)) {
         s_fail = k * BEOR_TB + j + 1;
       } else {
-        double l = sqrt(d);
-        A[pk(j, j)] = make_double2(l, 0.0);
-        if (k * BEOR_TB + j < pr.n) ld += 2.0 * log(l);
+        A[pk(j, j)] = make_double2(sqrt(d), 0.0);
       }
     }
     __syncthreads();
@@ -195,14 +192,14 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
       col[i] = a;
     }
     __syncthreads();
+    // rank-1 update of the trailing lower triangle: A_il -= L_ij conj(L_lj), 4 FMAs each
     for (int i = j + 1 + warp; i < BEOR_TB; i += nwarp) {
-      double2 ai = col[i];
+      const double2 ai = col[i];
       for (int l = j + 1 + lane; l <= i; l += 32) {
-        double2 al = col[l];
+        const double2 al = col[l];
         double2 x = A[pk(i, l)];
-        // x -= ai * conj(al)
-        x.x -= ai.x * al.x + ai.y * al.y;
-        x.y -= ai.y * al.x - ai.x * al.y;
+        x.x = fma(-ai.x, al.x, fma(-ai.y, al.y, x.x));
+        x.y = fma(-ai.y, al.x, fma(ai.x, al.y, x.y));
         A[pk(i, l)] = x;
       }
     }
@@ -212,40 +209,49 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
     if (tid == 0) v.status[p] = s_fail;
     return;
   }
-  if (tid == 0) v.logdet_sigma[p] += ld;
+  // log-determinant contribution, 2 sum ln L_jj over the real rows, in parallel
+  {
+    __shared__ double red[32];
+    double ldp = 0.0;
+    if (tid < BEOR_TB && k * BEOR_TB + tid < pr.n) ldp = 2.0 * log(A[pk(tid, tid)].x);
+    for (int o = 16; o > 0; o >>= 1) ldp += __shfl_xor_sync(0xffffffffu, ldp, o);
+    if (lane == 0) red[warp] = ldp;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < nwarp; ++w) s += red[w];
+      v.logdet_sigma[p] += s;
+    }
+  }
   // L_kk back to the workspace tile (upper part zero)
   for (int e = tid; e < BEOR_TILE_ELEMS; e += nthr) {
     int r = e % BEOR_TB, c = e / BEOR_TB;
     ws_store(ws + e, r >= c ? A[pk(r, c)] : make_double2(0.0, 0.0));
   }
   __syncthreads();
-  // in-place inverse, row by row: Linv[i][j] = -(sum_{m=j}^{i-1} L[i][m] Linv[m][j]) / L[i][i]
+  // in-place inverse, row by row: Linv[i][j] = -(sum_{m=j}^{i-1} L[i][m] Linv[m][j]) / L[i][i];
+  // four threads share each dot product (thread = 4 j + part)
+  const int jj = tid >> 2, part = tid & 3;
   for (int i = 0; i < BEOR_TB; ++i) {
     const double lii = A[pk(i, i)].x;
-    double2 t = make_double2(0.0, 0.0);
-    if (tid < i) {
-      const int j = tid;
-      double sr0 = 0.0, si0 = 0.0, sr1 = 0.0, si1 = 0.0;   // two chains each
-      int m = j;
-      for (; m + 1 < i; m += 2) {
-        const double2 a = A[pk(i, m)], b = A[pk(m, j)];
-        const double2 c = A[pk(i, m + 1)], d = A[pk(m + 1, j)];
-        sr0 = fma(a.x, b.x, fma(-a.y, b.y, sr0));
-        si0 = fma(a.x, b.y, fma(a.y, b.x, si0));
-        sr1 = fma(c.x, d.x, fma(-c.y, d.y, sr1));
-        si1 = fma(c.x, d.y, fma(c.y, d.x, si1));
+    double sr = 0.0, si = 0.0;
+    if (jj < i) {
+      for (int m = jj + part; m < i; m += 4) {
+        const double2 a = A[pk(i, m)], b = A[pk(m, jj)];
+        sr = fma(a.x, b.x, fma(-a.y, b.y, sr));
+        si = fma(a.x, b.y, fma(a.y, b.x, si));
       }
-      if (m < i) {
-        const double2 a = A[pk(i, m)], b = A[pk(m, j)];
-        sr0 = fma(a.x, b.x, fma(-a.y, b.y, sr0));
-        si0 = fma(a.x, b.y, fma(a.y, b.x, si0));
-      }
-      const double inv = 1.0 / lii;
-      t = make_double2(-(sr0 + sr1) * inv, -(si0 + si1) * inv);
     }
+    sr += __shfl_xor_sync(0xffffffffu, sr, 1);
+    si += __shfl_xor_sync(0xffffffffu, si, 1);
+    sr += __shfl_xor_sync(0xffffffffu, sr, 2);
+    si += __shfl_xor_sync(0xffffffffu, si, 2);
     __syncthreads();
-    if (tid < i) A[pk(i, tid)] = t;
-    if (tid == i) A[pk(i, i)] = make_double2(1.0 / lii, 0.0);
+    if (jj < i && part == 0) {
+      const double inv = 1.0 / lii;
+      A[pk(i, jj)] = make_double2(-sr * inv, -si * inv);
+    }
+    if (tid == 0) A[pk(i, i)] = make_double2(1.0 / lii, 0.0);
     __syncthreads();
   }
   double2* dinv = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
