@@ -18,7 +18,7 @@ using namespace beor;
 
 namespace {
 
-constexpr int kRefineIters = 2;   // refinement steps of the mixed solve (fixed: graph-captured)
+constexpr int kRefineIters = 1;   // refinement steps of the mixed solve (fixed: graph-captured)
 constexpr int kClasses = 8;       // kernel classes timed when profiling is on
 enum { KC_INIT = 0, KC_DIAG, KC_SLICE, KC_PANEL, KC_TRAIL, KC_SOLVE, KC_REFINE, KC_LNL };
 bool g_profiling = false;

@@ -10,6 +10,7 @@
 //  * panel/trail:   float64 tile GEMMs (the float64 comparator path);
 //  * solve:         blocked forward / backward substitution;
 //  * lnl:           q = Re(dbar^H abar) and lnL.
+#include <algorithm>
 #include <cmath>
 
 #include "beor_common.cuh"
@@ -91,30 +92,31 @@ __global__ void prior_kernel(BatchView v) {
 }
 
 template <typename WS>
-__global__ void init_ws_kernel(BatchView v) {
+__global__ void __launch_bounds__(256) init_ws_kernel(BatchView v) {
   const int p = blockIdx.y;
   const Prob pr = v.prob[p];
   const SetDesc sd = v.sets[pr.set];
-  WS* ws = reinterpret_cast<WS*>(v.ws) + pr.ws_off;
-  const int64_t total = tri_count(pr.nt) * BEOR_TILE_ELEMS;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    double2 m = sd.M[e];
-    int64_t t = e / BEOR_TILE_ELEMS;
-    int w = (int)(e % BEOR_TILE_ELEMS);
-    int r = w % BEOR_TB, c = w / BEOR_TB;
+  const int64_t ntiles = tri_count(pr.nt);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int I, J;
     tile_of(t, I, J);
-    if (I == J && r == c) {
-      m.x += v.phi_inv[pr.row_off + I * BEOR_TB + r];
-      m.y = 0.0;
+    const double2* __restrict__ src = sd.M + t * BEOR_TILE_ELEMS;
+    WS* __restrict__ dst = reinterpret_cast<WS*>(v.ws) + pr.ws_off + t * BEOR_TILE_ELEMS;
+    const double* pinv = v.phi_inv + pr.row_off + (int64_t)I * BEOR_TB;
+    for (int e = threadIdx.x; e < BEOR_TILE_ELEMS; e += blockDim.x) {
+      double2 m = __ldcs(src + e);
+      if (I == J && (e % BEOR_TB) == (e / BEOR_TB)) {
+        m.x += pinv[e % BEOR_TB];
+        m.y = 0.0;
+      }
+      ws_store(dst + e, m);
     }
-    ws_store(ws + e, m);
   }
 }
 
 cudaError_t launch_prior_init(const BatchView& v, bool mixed, cudaStream_t s) {
   prior_kernel<<<v.P, 256, 0, s>>>(v);
-  dim3 g(512, v.P);
+  dim3 g((unsigned)std::min<int64_t>(tri_count(v.max_nt), 1024), v.P);
   if (mixed)
     init_ws_kernel<float4><<<g, 256, 0, s>>>(v);
   else

@@ -22,10 +22,10 @@
 // Kernel structure (one CTA per SM, persistent over output tiles of 128 rows
 // x 64 complex columns): warp 0 issues TMA loads of the slice planes into a
 // 3-stage shared-memory ring (32-byte swizzle, K chunks of 16), warp 1 issues
-// the tcgen05.mma instructions (M = 128, N = 64, K = 16, bf16 -> fp32) into
-// eight TMEM accumulators (4 levels x re/im, all 512 columns), warps 2-5 drain
-// TMEM and apply
-// the update.  Every wait is bounded by a %globaltimer deadline; on expiry
+// the tcgen05.mma instructions (M = 128, N = 64..256, K = 16, bf16 -> fp32)
+// into eight TMEM accumulators (4 levels x re/im, all 512 columns), and
+// warps 2-9 (two per TMEM lane quarter, each with half the columns) drain
+// TMEM and apply the update.  Every wait is bounded by a %globaltimer deadline; on expiry
 // the kernel records an error code, drains what it issued and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -46,7 +46,8 @@ constexpr int MX_A_BYTES = BEOR_NPLANE * MX_M * MX_KC * 2;   // 40960
 constexpr int MX_B_BYTES = BEOR_NPLANE * MX_N * MX_KC * 2;   // 20480
 constexpr int MX_STAGE_BYTES = MX_A_BYTES + MX_B_BYTES;      // 61440
 constexpr int MX_SMEM = MX_STAGES * MX_STAGE_BYTES + 1024 + 256;
-constexpr int MX_THREADS = 192;
+constexpr int MX_EPI_WARPS = 8;        // two warps per TMEM lane quarter, each draining half the columns
+constexpr int MX_THREADS = 64 + 32 * MX_EPI_WARPS;
 constexpr uint32_t MX_TMEM_COLS = 512;
 constexpr unsigned long long MX_TIMEOUT_NS = 2000000000ull;
 
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       mbar_init(empty_bar(s), 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 128);
+    mbar_init(acc_empty, 32 * MX_EPI_WARPS);
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -354,9 +355,10 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       mbar_wait_deadline(drain, 0);
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
+    // ---------------- epilogue (warps 2..9) ----------------
     const int lane_base = 32 * (warp & 3);
     const int r = lane_base + lane;   // output row within the tile
+    const int cbeg = ((warp - 2) >> 2) * (MX_N / 2), cend = cbeg + MX_N / 2;   // this warp's columns
     uint32_t tcount = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
       TileJob jb = decode_tile(v, prefix, t, k, MODE);
@@ -379,12 +381,12 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       float4 cv[EC], cn[EC];
       if (MODE == MODE_TRAIL) {
 #pragma unroll
-        for (int q = 0; q < EC; ++q) cv[q] = __ldcs(C + (int64_t)q * BEOR_TB);
+        for (int q = 0; q < EC; ++q) cv[q] = __ldcs(C + (int64_t)(cbeg + q) * BEOR_TB);
       }
 #pragma unroll 1
-      for (int c0 = 0; c0 < MX_N; c0 += EC) {
+      for (int c0 = cbeg; c0 < cend; c0 += EC) {
         // prefetch the next chunk of the working matrix while this one is processed
-        if (MODE == MODE_TRAIL && c0 + EC < MX_N) {
+        if (MODE == MODE_TRAIL && c0 + EC < cend) {
 #pragma unroll
           for (int q = 0; q < EC; ++q) cn[q] = __ldcs(C + (int64_t)(c0 + EC + q) * BEOR_TB);
         }
