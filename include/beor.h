@@ -37,7 +37,8 @@
  *    std::complex<double> / numpy complex128); matrices are row-major.
  *  - Per-point status: 0 = ok; j > 0 = Sigma not positive definite at
  *    1-based column j (lnL = -inf); -1 = iterative refinement of the solve
- *    did not reach its tolerance (lnL still returned).
+ *    did not converge (last correction above 1e-4 of the solution; lnL
+ *    still returned).
  */
 #ifndef BEOR_H
 #define BEOR_H
@@ -136,7 +137,7 @@ int beor_get_dbar(beor_ctx *ctx, beor_c128 *dbar_out);
  * captures a batch's graph. */
 typedef struct {
   int refine_iters_max;     /* refinement steps taken */
-  double resid_rel_max;     /* largest final ||dbar - Sigma x|| / ||dbar|| */
+  double resid_rel_max;     /* largest last refinement correction ||d|| / ||x|| */
   double ms_last;           /* device time of the last batched evaluation */
   int64_t kernel_launches;  /* kernels launched by the last batched evaluation */
   double ms_class[8];

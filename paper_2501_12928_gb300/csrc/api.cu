@@ -18,7 +18,7 @@ using namespace beor;
 
 namespace {
 
-constexpr int kRefineIters = 1;   // refinement steps of the mixed solve (fixed: graph-captured)
+constexpr int kRefineIters = 2;   // refinement steps of the mixed solve (fixed: graph-captured)
 constexpr int kClasses = 8;       // kernel classes timed when profiling is on
 enum { KC_INIT = 0, KC_DIAG, KC_SLICE, KC_PANEL, KC_TRAIL, KC_SOLVE, KC_REFINE, KC_LNL };
 bool g_profiling = false;
@@ -203,8 +203,6 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
       RUN(KC_REFINE, launch_refine_update(v, s));
       L += 4 + solve_launch_count(pl.max_nt);
     }
-    RUN(KC_REFINE, launch_residual(v, s));
-    L += 3;
   }
   RUN(KC_LNL, launch_lnl(v, s));
   L += 1;

@@ -91,13 +91,15 @@ __global__ void prior_kernel(BatchView v) {
   }
 }
 
+// grid (problem, tile): problems fastest, so the problems of one instrument
+// read each tile of M from L2 rather than from HBM
 template <typename WS>
 __global__ void __launch_bounds__(256) init_ws_kernel(BatchView v) {
-  const int p = blockIdx.y;
+  const int p = blockIdx.x;
   const Prob pr = v.prob[p];
   const SetDesc sd = v.sets[pr.set];
   const int64_t ntiles = tri_count(pr.nt);
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (int64_t t = blockIdx.y; t < ntiles; t += gridDim.y) {
     int I, J;
     tile_of(t, I, J);
     const double2* __restrict__ src = sd.M + t * BEOR_TILE_ELEMS;
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(256) init_ws_kernel(BatchView v) {
 
 cudaError_t launch_prior_init(const BatchView& v, bool mixed, cudaStream_t s) {
   prior_kernel<<<v.P, 256, 0, s>>>(v);
-  dim3 g((unsigned)std::min<int64_t>(tri_count(v.max_nt), 1024), v.P);
+  dim3 g(v.P, (unsigned)std::min<int64_t>(tri_count(v.max_nt), 65535));
   if (mixed)
     init_ws_kernel<float4><<<g, 256, 0, s>>>(v);
   else

@@ -630,14 +630,15 @@ __global__ void resid_init_kernel(BatchView v) {
   }
 }
 
-// One CTA per (lower tile of M, problem): r_I -= M_IJ x_J and, off the
-// diagonal, r_J -= M_IJ^H x_I, accumulated with float64 atomics.
+// One CTA per (problem, lower tile of M) -- problems fastest, so the problems
+// of one instrument share each M tile through L2: r_I -= M_IJ x_J and, off
+// the diagonal, r_J -= M_IJ^H x_I, accumulated with float64 atomics.
 __global__ void __launch_bounds__(128) resid_tile_kernel(BatchView v) {
   __shared__ double2 xj[BEOR_TB], xi[BEOR_TB];
-  const int p = blockIdx.y;
+  const int p = blockIdx.x;
   const Prob pr = v.prob[p];
   const SetDesc sd = v.sets[pr.set];
-  const int64_t t = blockIdx.x;
+  const int64_t t = blockIdx.y;
   if (t >= tri_count(pr.nt) || v.status[p] > 0) return;
   int I, J;
   {
@@ -715,34 +716,61 @@ __global__ void resid_norm_kernel(BatchView v) {
       sa += red[0][w];
       sb += red[1][w];
     }
-    double rel = sb > 0.0 ? sqrt(sa / sb) : 0.0;
-    v.resid[p] = rel;
-    if (v.status[p] == 0 && !(rel <= 1e-10)) v.status[p] = -1;
-    if (v.status[p] == -1 && rel <= 1e-10) v.status[p] = 0;
+    v.resid[p] = sb > 0.0 ? sqrt(sa / sb) : 0.0;
   }
 }
 
 cudaError_t launch_residual(const BatchView& v, cudaStream_t s) {
   resid_init_kernel<<<dim3(8, v.P), 256, 0, s>>>(v);
   int64_t tiles = tri_count(v.max_nt);
-  resid_tile_kernel<<<dim3((unsigned)tiles, v.P), 128, 0, s>>>(v);
+  resid_tile_kernel<<<dim3(v.P, (unsigned)tiles), 128, 0, s>>>(v);
   resid_norm_kernel<<<v.P, 256, 0, s>>>(v);
   return cudaGetLastError();
 }
 
+// x += d for every problem; one CTA per problem.  The relative size of the
+// correction, ||d|| / ||x||, is the convergence measure: the error left after
+// the step is about rho ||d||, with rho ~ kappa * 2^-39 << 1 the contraction
+// of the refinement for the slice factor, so a correction below 1e-4 of x
+// leaves an error far below every tolerance, while a failing factorisation
+// (rho ~ 1) produces corrections of the size of x.  Larger -> status -1.
 __global__ void refine_update_kernel(BatchView v) {
-  const int p = blockIdx.y;
+  const int p = blockIdx.x;
   const Prob pr = v.prob[p];
   if (v.status[p] > 0) return;
+  __shared__ double red[2][32];
   const int np = pr.nt * BEOR_TB;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += gridDim.x * blockDim.x) {
-    double2 x = v.vec_x[pr.row_off + j], d = v.vec_d[pr.row_off + j];
-    v.vec_x[pr.row_off + j] = make_double2(x.x + d.x, x.y + d.y);
+  double a = 0.0, b = 0.0;
+  for (int j = threadIdx.x; j < np; j += blockDim.x) {
+    const double2 x = v.vec_x[pr.row_off + j], d = v.vec_d[pr.row_off + j];
+    const double2 y = make_double2(x.x + d.x, x.y + d.y);
+    v.vec_x[pr.row_off + j] = y;
+    a += d.x * d.x + d.y * d.y;
+    b += y.x * y.x + y.y * y.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sa += red[0][w];
+      sb += red[1][w];
+    }
+    const double rel = sb > 0.0 ? sqrt(sa / sb) : 0.0;
+    v.resid[p] = rel;
+    v.status[p] = rel <= 1e-4 ? 0 : -1;
   }
 }
 
 cudaError_t launch_refine_update(const BatchView& v, cudaStream_t s) {
-  refine_update_kernel<<<dim3(8, v.P), 256, 0, s>>>(v);
+  refine_update_kernel<<<v.P, 256, 0, s>>>(v);
   return cudaGetLastError();
 }
 
