@@ -355,8 +355,11 @@ def _lnl_multi_dev(P, likes, dev_phi, out, sts):
 
 
 def _traffic_per_launch(tiles_per_launch):
-    """DRAM bytes per trailing launch from the committed ncu summary, if any."""
-    path = os.path.join(ROOT, "profiles", "slice_gemm_trail_C3.md")
+    """DRAM bytes per trailing launch from the committed ncu summary, if any:
+    the per-tile DRAM bytes measured on the 3280-mode case (traffic per tile
+    is the working-matrix read-modify-write, the same at every size) times
+    the tiles of an average launch."""
+    path = os.path.join(ROOT, "profiles", "slice_gemm_trail_C1_B8.md")
     try:
         with open(path) as f:
             for line in f:
