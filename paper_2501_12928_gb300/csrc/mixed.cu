@@ -121,6 +121,11 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
       : "memory");
 }
+// Bulk prefetch of a contiguous global range into L2 (size a multiple of 16 bytes).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)), "r"(bytes)
+               : "memory");
+}
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -174,6 +179,23 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t negate_a, uint32_t n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (negate_a << 13) | ((n >> 3) << 17) |
          ((uint32_t)(MX_M >> 4) << 24);
+}
+
+// Sum of the four level accumulators as a double-float number.  Levels 0-2
+// hold exact fp32 values (integers times 2^0, 2^-8, 2^-16 units), level 3 is
+// rounded and about 2^-24 below level 0: two exact two-sums, then the small
+// terms into the low part.
+__device__ __forceinline__ dfl levels_sum(float l0, float l1, float l2, float l3) {
+  const dfl a = df_two_sum(l0, l1);
+  const dfl b = df_two_sum(a.hi, l2);
+  return df_fast_two_sum(b.hi, b.lo + (a.lo + l3));
+}
+// a - b for double-float numbers with |a.lo|, |b.lo| below half an ulp of
+// their high parts: one exact two-sum of the high parts, the low parts added
+// in fp32 (relative error ~2^-44), renormalised.
+__device__ __forceinline__ dfl df_sub_quick(dfl a, dfl b) {
+  const dfl s = df_two_sum(a.hi, -b.hi);
+  return df_fast_two_sum(s.hi, s.lo + (a.lo - b.lo));
 }
 
 // ---------------------------------------------------------------------------
@@ -269,6 +291,12 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         const int a_row = (int)(pr.row_off + (int64_t)jb.i * BEOR_TB);
         const int b_row = MODE == MODE_TRAIL ? (int)(pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N)
                                              : jb.p * BEOR_TB + jb.h * MX_N;
+        if (MODE == MODE_TRAIL) {
+          // the epilogue will read this tile's 64 working-matrix columns (128 KB, contiguous)
+          const float4* ct = reinterpret_cast<const float4*>(v.ws) + pr.ws_off +
+                             tri_index(jb.i, jb.j) * BEOR_TILE_ELEMS + (int64_t)(jb.h * MX_N) * BEOR_TB;
+          prefetch_l2(ct, (uint32_t)(MX_N * BEOR_TB * sizeof(float4)));
+        }
         for (int kc = 0; kc < BEOR_TB / MX_KC; ++kc, ++it) {
           const int s = it % MX_STAGES;
           const uint32_t ph = (it / MX_STAGES) & 1;
@@ -405,15 +433,15 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           ex = max(-250, min(250, ex));
           const int e1 = ex >> 1, e2 = ex - e1;   // two exact power-of-two factors
           const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
-          dfl vr = df_add(df_two_sum(lr[0][q], lr[1][q]), df_two_sum(lr[2][q], lr[3][q]));
-          dfl vi = df_add(df_two_sum(li[0][q], li[1][q]), df_two_sum(li[2][q], li[3][q]));
+          dfl vr = levels_sum(lr[0][q], lr[1][q], lr[2][q], lr[3][q]);
+          dfl vi = levels_sum(li[0][q], li[1][q], li[2][q], li[3][q]);
           vr.hi = vr.hi * s1 * s2; vr.lo = vr.lo * s1 * s2;
           vi.hi = vi.hi * s1 * s2; vi.lo = vi.lo * s1 * s2;
           float4* cp = C + (int64_t)(c0 + q) * BEOR_TB;
           if (MODE == MODE_TRAIL) {
             const float4 w = cv[q];
-            const dfl wr = df_add(dfl{w.x, w.y}, df_neg(vr));
-            const dfl wi = df_add(dfl{w.z, w.w}, df_neg(vi));
+            const dfl wr = df_sub_quick(dfl{w.x, w.y}, vr);
+            const dfl wi = df_sub_quick(dfl{w.z, w.w}, vi);
             __stcs(cp, make_float4(wr.hi, wr.lo, wi.hi, wi.lo));
           } else {
             __stcs(cp, make_float4(vr.hi, vr.lo, vi.hi, vi.lo));
