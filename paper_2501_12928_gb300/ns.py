@@ -200,7 +200,8 @@ class NestedSampler:
             live_l[worst] = new_l
             it += 1
             lmax = float(live_l.max())
-            if logz > -math.inf and math.log1p(math.exp(lmax + logx - logz)) < math.log1p(self.stop_frac):
+            # remaining mass L_max X below stop_frac of Z (compared in logs: no overflow)
+            if logz > -math.inf and lmax + logx - logz < math.log(self.stop_frac):
                 break
             if self.checkpoint and it % self.checkpoint_every == 0:
                 st.update(live=live, live_l=live_l, logz=logz, logx=logx, h=h, it=it)
