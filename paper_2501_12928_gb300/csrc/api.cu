@@ -86,7 +86,7 @@ struct beor_ctx {
   DevBuf d, w;
   // precompute
   bool have_pre = false;
-  DevBuf M, dbar;
+  DevBuf M, dbar, Mdf;
   // bookkeeping
   beor_stats stats{};
   Plan* last_plan = nullptr;
@@ -230,6 +230,7 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, Plan** out) {
     sd.n_k = c->n_k;
     sd.lssm_prior_var = c->lssm_prior_var;
     sd.M = c->M.as<double2>();
+    sd.Mdf = c->Mdf.as<float4>();
     sd.dbar = c->dbar.as<double2>();
     sd.kbin = c->kbin.as<int32_t>();
     pl->phi_off.push_back(phi_total);
@@ -526,6 +527,11 @@ int beor_precompute(beor_ctx* c, void* stream) {
                                c->w.as<double>(), c->d.as<double2>(), c->n, c->nt, G.as<double2>(), u.as<double2>(),
                                c->M.as<double2>(), c->dbar.as<double2>(), s));
     CKC(c, cudaStreamSynchronize(s));
+  }
+  if (c->precision == BEOR_PREC_MIXED) {
+    const int64_t ne = tri_count(c->nt) * BEOR_TILE_ELEMS;
+    CKC(c, c->Mdf.alloc(sizeof(float4) * (size_t)ne));
+    CKC(c, split_double_float(c->M.as<double2>(), ne, c->Mdf.as<float4>(), s));
   }
   CKC(c, cudaStreamSynchronize(s));
   c->have_pre = true;

@@ -40,6 +40,7 @@ struct SetDesc {
   int n, nt, n_k;
   double lssm_prior_var;
   const double2* M;       // packed tiles (float64), lower
+  const float4* Mdf;      // the same as double-float pairs (mixed contexts), or null
   const double2* dbar;    // Np
   const int32_t* kbin;    // n
   const double* phi;      // B x n_k (device staging)

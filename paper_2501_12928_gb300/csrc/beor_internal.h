@@ -9,6 +9,7 @@
 namespace beor {
 
 // precompute.cu
+cudaError_t split_double_float(const double2* M, int64_t n, float4* out, cudaStream_t s);
 cudaError_t precompute_dense(const double2* T, int64_t n_vis, int n, int64_t ld, const double* w,
                              const double2* d, int nt, double2* Mt, double2* dbar, cudaStream_t s);
 cudaError_t precompute_factored(const double2* A, const double2* W, int nf, int64_t ntb, int ncells,

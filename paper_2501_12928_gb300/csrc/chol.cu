@@ -92,9 +92,8 @@ __global__ void prior_kernel(BatchView v) {
 }
 
 // grid (problem, tile): problems fastest, so the problems of one instrument
-// read each tile of M from L2 rather than from HBM
-template <typename WS>
-__global__ void __launch_bounds__(256) init_ws_kernel(BatchView v) {
+// read each tile of M from L2 rather than from HBM.  Float64 path: M as is.
+__global__ void __launch_bounds__(256) init_ws_f64_kernel(BatchView v) {
   const int p = blockIdx.x;
   const Prob pr = v.prob[p];
   const SetDesc sd = v.sets[pr.set];
@@ -103,15 +102,40 @@ __global__ void __launch_bounds__(256) init_ws_kernel(BatchView v) {
     int I, J;
     tile_of(t, I, J);
     const double2* __restrict__ src = sd.M + t * BEOR_TILE_ELEMS;
-    WS* __restrict__ dst = reinterpret_cast<WS*>(v.ws) + pr.ws_off + t * BEOR_TILE_ELEMS;
+    double2* __restrict__ dst = reinterpret_cast<double2*>(v.ws) + pr.ws_off + t * BEOR_TILE_ELEMS;
     const double* pinv = v.phi_inv + pr.row_off + (int64_t)I * BEOR_TB;
     for (int e = threadIdx.x; e < BEOR_TILE_ELEMS; e += blockDim.x) {
-      double2 m = __ldcs(src + e);
+      double2 m = src[e];
       if (I == J && (e % BEOR_TB) == (e / BEOR_TB)) {
         m.x += pinv[e % BEOR_TB];
         m.y = 0.0;
       }
-      ws_store(dst + e, m);
+      dst[e] = m;
+    }
+  }
+}
+
+// Mixed path: copy the double-float M; the diagonal gets Phi^-1 in
+// double-float arithmetic (no float64 instruction per element).
+__global__ void __launch_bounds__(256) init_ws_df_kernel(BatchView v) {
+  const int p = blockIdx.x;
+  const Prob pr = v.prob[p];
+  const SetDesc sd = v.sets[pr.set];
+  const int64_t ntiles = tri_count(pr.nt);
+  for (int64_t t = blockIdx.y; t < ntiles; t += gridDim.y) {
+    int I, J;
+    tile_of(t, I, J);
+    const float4* __restrict__ src = sd.Mdf + t * BEOR_TILE_ELEMS;
+    float4* __restrict__ dst = reinterpret_cast<float4*>(v.ws) + pr.ws_off + t * BEOR_TILE_ELEMS;
+    for (int e = threadIdx.x; e < BEOR_TILE_ELEMS; e += blockDim.x) dst[e] = src[e];
+    if (I != J) continue;                 // uniform per CTA
+    __syncthreads();                      // the copy of every diagonal element has landed
+    if (threadIdx.x < BEOR_TB) {
+      const int r = threadIdx.x;
+      const int e = r * BEOR_TB + r;
+      const float4 m = src[e];
+      const dfl w = df_add(dfl{m.x, m.y}, df_from_double(v.phi_inv[pr.row_off + (int64_t)I * BEOR_TB + r]));
+      dst[e] = make_float4(w.hi, w.lo, 0.0f, 0.0f);
     }
   }
 }
@@ -120,9 +144,9 @@ cudaError_t launch_prior_init(const BatchView& v, bool mixed, cudaStream_t s) {
   prior_kernel<<<v.P, 256, 0, s>>>(v);
   dim3 g(v.P, (unsigned)std::min<int64_t>(tri_count(v.max_nt), 65535));
   if (mixed)
-    init_ws_kernel<float4><<<g, 256, 0, s>>>(v);
+    init_ws_df_kernel<<<g, 256, 0, s>>>(v);
   else
-    init_ws_kernel<double2><<<g, 256, 0, s>>>(v);
+    init_ws_f64_kernel<<<g, 256, 0, s>>>(v);
   return cudaGetLastError();
 }
 
@@ -612,23 +636,37 @@ __global__ void __launch_bounds__(256) bwd_step_kernel(BatchView v, int k, doubl
     xki[tid] = df_from_double(q.y);
   }
   __syncthreads();
+  // r_i[c] -= sum_m conj(L_ki[m][c]) x_k[m]: tile (k, i) column-major, so each
+  // column is contiguous.  Two passes of 64 columns through shared memory
+  // (row stride 129 elements: conflict-free column reads); thread (c, part)
+  // sums a quarter of m, four partial sums per column.
+  extern __shared__ __align__(16) unsigned char bsm_raw[];
+  WS* sm = reinterpret_cast<WS*>(bsm_raw);
+  CAcc* part_acc = reinterpret_cast<CAcc*>(bsm_raw + sizeof(WS) * 64 * 129);
   const WS* t = reinterpret_cast<const WS*>(v.ws) + pr.ws_off + tri_index(k, i) * BEOR_TILE_ELEMS;
-  const int warp = tid >> 5, lane = tid & 31;
-  for (int c = warp; c < BEOR_TB; c += 8) {
+  const int cc = tid & 63, part = tid >> 6;
+  for (int h = 0; h < 2; ++h) {
+    const WS* src = t + (int64_t)(64 * h) * BEOR_TB;
+    for (int e = tid; e < 64 * BEOR_TB; e += 256) sm[(e >> 7) * 129 + (e & 127)] = src[e];
+    __syncthreads();
     CAcc a;
     cacc_zero(a);
+#pragma unroll 4
+    for (int m = part * 32; m < part * 32 + 32; ++m) cacc_mac(a, sm + cc * 129 + m, xk[m], xkr[m], xki[m], true);
+    part_acc[tid] = a;
+    __syncthreads();
+    if (part == 0) {
 #pragma unroll
-    for (int m = lane; m < BEOR_TB; m += 32) cacc_mac(a, t + c * BEOR_TB + m, xk[m], xkr[m], xki[m], true);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cacc_add(a, cacc_shfl_xor(a, o));
-    if (lane == 0) {
-      const double2 s = cacc_get(a, t);
+      for (int q = 1; q < 4; ++q) cacc_add(a, part_acc[cc + 64 * q]);
+      const double2 sv = cacc_get(a, t);
+      const int c = 64 * h + cc;
       double2 cur = r[i * BEOR_TB + c];
-      cur.x -= s.x;
-      cur.y -= s.y;
+      cur.x -= sv.x;
+      cur.y -= sv.y;
       r[i * BEOR_TB + c] = cur;
       rk[c] = cur;
     }
+    __syncthreads();
   }
   if (i != k - 1) return;
   __syncthreads();
@@ -637,15 +675,22 @@ __global__ void __launch_bounds__(256) bwd_step_kernel(BatchView v, int k, doubl
   if (tid < BEOR_TB) x[i * BEOR_TB + tid] = xk[tid];
 }
 
+constexpr size_t kBwdSmem = 16 * 64 * 129 + sizeof(CAcc) * 256;
+
 template <typename WS>
 static cudaError_t solve_impl(const BatchView& v, const double2* rhs, double2* out, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(bwd_step_kernel<WS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+    attr = true;
+  }
   const int nt = v.max_nt;
   fwd_step_kernel<WS><<<dim3(nt, v.P), 256, 0, s>>>(v, -1, rhs);
   for (int k = 0; k + 1 < nt; ++k) fwd_step_kernel<WS><<<dim3(nt - k - 1, v.P), 256, 0, s>>>(v, k, rhs);
-  bwd_step_kernel<WS><<<dim3(nt, v.P), 256, 0, s>>>(v, nt, out);
+  bwd_step_kernel<WS><<<dim3(nt, v.P), 256, kBwdSmem, s>>>(v, nt, out);
   for (int k = nt - 1; k >= 1; --k) {
     // problems whose last block is k-1 (nt_p == k) start here
-    bwd_step_kernel<WS><<<dim3(k, v.P), 256, 0, s>>>(v, k, out);
+    bwd_step_kernel<WS><<<dim3(k, v.P), 256, kBwdSmem, s>>>(v, k, out);
   }
   return cudaGetLastError();
 }

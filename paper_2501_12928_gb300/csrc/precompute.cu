@@ -183,8 +183,22 @@ __global__ void assemble_dbar_kernel(const double2* __restrict__ u, const double
   dbar[j] = make_double2(vr, vi);
 }
 
+// x -> (hi, lo) float pairs with hi + lo = x to ~48 bits (once per precompute)
+__global__ void split_df_kernel(const double2* __restrict__ M, int64_t n, float4* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = M[e];
+    const float rh = (float)v.x, ih = (float)v.y;
+    out[e] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host launchers
+cudaError_t split_double_float(const double2* M, int64_t n, float4* out, cudaStream_t s) {
+  split_df_kernel<<<1024, 256, 0, s>>>(M, n, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 cudaError_t precompute_dense(const double2* T, int64_t n_vis, int n, int64_t ld, const double* w,
                              const double2* d, int nt, double2* Mt, double2* dbar, cudaStream_t s) {
