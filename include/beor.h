@@ -146,9 +146,21 @@ typedef struct {
 int beor_get_stats(const beor_ctx *ctx, beor_stats *out);
 
 /* Process-wide switch: when on, batched evaluations record a CUDA event
- * before every kernel (inside the captured graph) and report per-class
- * device times in beor_stats.  Costs a few microseconds per kernel. */
+ * before and after every kernel (inside the captured graph, on the kernel's
+ * own stream) and report per-class device times in beor_stats; under the
+ * look-ahead schedule launches of different classes overlap, so the class
+ * times add up to more than ms_last.  Costs a few microseconds per kernel. */
 int beor_set_profiling(int on);
+
+/* Process-wide switch of the mixed-precision factorisation schedule (default
+ * on).  On: look-ahead -- block step k's trailing update is split into the
+ * next block column and the rest; the rest runs on a second, low-priority
+ * stream while the diagonal block, slicing and panel of step k + 1 run at high
+ * priority (the same blocked right-looking Cholesky, reordered as a task
+ * graph: every tile sees the same operations, so the results are identical).
+ * Off: one stream, steps in order.
+ * Float64 contexts always use the in-order schedule. */
+int beor_set_lookahead(int on);
 
 /* Per-point log-determinant pieces of the last beor_lnl call on ctx (B
  * values each, host memory): log|Phi|, log|Sigma| and q = dbar^H abar. */

@@ -13,5 +13,6 @@ from .beor import (  # noqa: F401
     PREC_FP64,
     PREC_MIXED,
     KERNEL_CLASSES,
+    set_lookahead,
     set_profiling,
 )

@@ -50,6 +50,7 @@ def _load():
         "beor_get_terms": [_P, _P, _P, _P, _c.c_int],
         "beor_get_factor": [_P, _c.c_int, _P],
         "beor_set_profiling": [_c.c_int],
+        "beor_set_lookahead": [_c.c_int],
         "beor_dbar_factored_noalloc": [_P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _P, _P, _P, _P],
         "beor_mlp_create": [_c.POINTER(_P), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64],
         "beor_mlp_destroy": [_P],
@@ -96,6 +97,10 @@ KERNEL_CLASSES = ("init", "diag", "slice", "panel", "trail", "solve", "refine", 
 
 def set_profiling(on: bool):
     _check(_lib().beor_set_profiling(1 if on else 0), "beor_set_profiling")
+
+
+def set_lookahead(on: bool):
+    _check(_lib().beor_set_lookahead(1 if on else 0), "beor_set_lookahead")
 
 
 def _stream(stream):

@@ -22,6 +22,7 @@ constexpr int kRefineIters = 2;   // refinement steps of the mixed solve (fixed:
 constexpr int kClasses = 8;       // kernel classes timed when profiling is on
 enum { KC_INIT = 0, KC_DIAG, KC_SLICE, KC_PANEL, KC_TRAIL, KC_SOLVE, KC_REFINE, KC_LNL };
 bool g_profiling = false;
+bool g_lookahead = true;
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -118,10 +119,17 @@ struct Plan {
   int64_t launches = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool prof = false;
+  bool lookahead = true;            // schedule of the mixed factorisation captured in the graph
+  int prio_hi = 0;                  // greatest stream priority of the device
   std::vector<cudaEvent_t> pev;     // boundary events (profiling)
   std::vector<int> pcls;            // class of the launch after each boundary event
+  cudaStream_t side = nullptr;      // second stream of the look-ahead schedule
+  cudaEvent_t ev_col = nullptr, ev_rest = nullptr;
   ~Plan() {
     for (cudaEvent_t e : pev) cudaEventDestroy(e);
+    if (ev_col) cudaEventDestroy(ev_col);
+    if (ev_rest) cudaEventDestroy(ev_rest);
+    if (side) cudaStreamDestroy(side);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (maps) mixed_maps_destroy(maps);
@@ -146,16 +154,18 @@ int fail_cuda(beor_ctx* c, cudaError_t e) {
     if (_e != cudaSuccess) return fail_cuda(ctx, _e); \
   } while (0)
 
-// The sequence of kernels of one batched evaluation.  With `mark` set,
-// an externally visible event is recorded before every launch (and one at
-// the end) so that each kernel class can be timed inside the graph.
+// The sequence of kernels of one batched evaluation.  With `mark` set, an
+// externally visible event is recorded on the launching stream before and
+// after every launch, so that each kernel class can be timed inside the graph
+// (launches on the two streams of the look-ahead schedule overlap, so the
+// class times add up to more than the evaluation's wall time).
 cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) {
   const BatchView& v = pl.view;
   int64_t L = 0;
   size_t ev_i = 0;
   cudaError_t e;
   if (mark) pl.pcls.clear();
-  auto tick = [&](int cls) -> cudaError_t {
+  auto tick = [&](cudaStream_t on) -> cudaError_t {
     if (!mark) return cudaSuccess;
     if (ev_i >= pl.pev.size()) {
       cudaEvent_t ev;
@@ -163,34 +173,81 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
       if (x != cudaSuccess) return x;
       pl.pev.push_back(ev);
     }
-    pl.pcls.push_back(cls);
-    return cudaEventRecordWithFlags(pl.pev[ev_i++], s, cudaEventRecordExternal);
+    return cudaEventRecordWithFlags(pl.pev[ev_i++], on, cudaEventRecordExternal);
   };
-#define RUN(cls, x)                   \
+#define RUN_ON(cls, on, x)            \
   do {                                \
-    e = tick(cls);                    \
+    if (mark) pl.pcls.push_back(cls); \
+    e = tick(on);                     \
     if (e != cudaSuccess) return e;   \
     e = (x);                          \
     if (e != cudaSuccess) return e;   \
+    e = tick(on);                     \
+    if (e != cudaSuccess) return e;   \
   } while (0)
+#define RUN(cls, x) RUN_ON(cls, s, x)
+  if (pl.mixed) {
+    e = mixed_reset_counters(pl.maps, s);
+    if (e != cudaSuccess) return e;
+  }
   RUN(KC_INIT, launch_prior_init(v, pl.mixed, s));
   L += 2;
   RUN(KC_INIT, launch_copy_dbar(v, s));
   L += 1;
-  for (int k = 0; k < pl.max_nt; ++k) {
-    RUN(KC_DIAG, launch_diag(v, k, pl.mixed, s));
+  if (pl.mixed && pl.lookahead) {
+    // Look-ahead schedule of the mixed factorisation (two streams):
+    //   main: col(k) -> diag(k+1) -> slice(k+1) -> panel(k+1) -> slice(k+1) -> [rest(k)] col(k+1) ...
+    //   side: [col(k)] rest(k)
+    // col(k) updates block column k+1 only, rest(k) the columns j >= k+2, so
+    // the float64 diagonal factorisation and the panel of step k+1 run at high
+    // priority on the SMs that rest(k) leaves free; rest(k) takes its tiles
+    // from a counter, so its CTAs that start late (after the high-priority
+    // kernels) just take fewer.
+    const int hi = pl.prio_hi;
+    RUN(KC_DIAG, launch_diag(v, 0, true, s, hi));
     L += 1;
-    if (k + 1 < pl.max_nt) {
-      if (pl.mixed) {
-        RUN(KC_SLICE, launch_slice_panel(v, k, s));
-        RUN(KC_PANEL, launch_panel_mixed(v, pl.maps, k, s));
-        RUN(KC_SLICE, launch_slice_panel(v, k, s));
-        RUN(KC_TRAIL, launch_trail_mixed(v, pl.maps, k, s));
-        L += 4;
-      } else {
-        RUN(KC_PANEL, launch_panel_f64(v, k, s));
-        RUN(KC_TRAIL, launch_trail_f64(v, k, s));
-        L += 2;
+    if (pl.max_nt > 1) {
+      RUN(KC_SLICE, launch_slice_panel(v, 0, s, hi));
+      RUN(KC_PANEL, launch_panel_mixed(v, pl.maps, 0, s, hi));
+      RUN(KC_SLICE, launch_slice_panel(v, 0, s, hi));
+      L += 3;
+    }
+    for (int k = 0; k + 1 < pl.max_nt; ++k) {
+      RUN(KC_TRAIL, launch_trail_mixed(v, pl.maps, k, TRAIL_NEXT_COL, s, hi));
+      L += 1;
+      if ((e = cudaEventRecord(pl.ev_col, s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(pl.side, pl.ev_col, 0)) != cudaSuccess) return e;
+      RUN(KC_DIAG, launch_diag(v, k + 1, true, s, hi));
+      L += 1;
+      if (mixed_tiles(pl.maps, 1, k) > 0) {
+        RUN_ON(KC_TRAIL, pl.side, launch_trail_mixed(v, pl.maps, k, TRAIL_REST, pl.side));
+        L += 1;
+      }
+      if ((e = cudaEventRecord(pl.ev_rest, pl.side)) != cudaSuccess) return e;
+      if (k + 2 < pl.max_nt) {
+        RUN(KC_SLICE, launch_slice_panel(v, k + 1, s, hi));
+        RUN(KC_PANEL, launch_panel_mixed(v, pl.maps, k + 1, s, hi));
+        RUN(KC_SLICE, launch_slice_panel(v, k + 1, s, hi));
+        L += 3;
+      }
+      if ((e = cudaStreamWaitEvent(s, pl.ev_rest, 0)) != cudaSuccess) return e;
+    }
+  } else {
+    for (int k = 0; k < pl.max_nt; ++k) {
+      RUN(KC_DIAG, launch_diag(v, k, pl.mixed, s));
+      L += 1;
+      if (k + 1 < pl.max_nt) {
+        if (pl.mixed) {
+          RUN(KC_SLICE, launch_slice_panel(v, k, s));
+          RUN(KC_PANEL, launch_panel_mixed(v, pl.maps, k, s));
+          RUN(KC_SLICE, launch_slice_panel(v, k, s));
+          RUN(KC_TRAIL, launch_trail_mixed(v, pl.maps, k, TRAIL_ALL, s));
+          L += 4;
+        } else {
+          RUN(KC_PANEL, launch_panel_f64(v, k, s));
+          RUN(KC_TRAIL, launch_trail_f64(v, k, s));
+          L += 2;
+        }
       }
     }
   }
@@ -206,9 +263,8 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
   }
   RUN(KC_LNL, launch_lnl(v, s));
   L += 1;
-  e = tick(-1);
-  if (e != cudaSuccess) return e;
 #undef RUN
+#undef RUN_ON
   if (nlaunch) *nlaunch = L;
   return cudaSuccess;
 }
@@ -269,8 +325,8 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, Plan** out) {
   chk(pl->scal.alloc(sizeof(double) * (size_t)pl->P * 6 + sizeof(int32_t) * pl->P));
   chk(pl->flags.alloc(sizeof(Flags)));
   if (pl->mixed) {
-    chk(pl->panel_sl.alloc(sizeof(__nv_bfloat16) * (size_t)BEOR_NPLANE * rows * BEOR_TB));
-    chk(pl->panel_exp.alloc(sizeof(int32_t) * (size_t)rows));
+    chk(pl->panel_sl.alloc(sizeof(__nv_bfloat16) * 2 * (size_t)BEOR_NPLANE * rows * BEOR_TB));
+    chk(pl->panel_exp.alloc(sizeof(int32_t) * 2 * (size_t)rows));
     chk(pl->linv_sl.alloc(sizeof(__nv_bfloat16) * (size_t)BEOR_NPLANE * pl->P * BEOR_TB * BEOR_TB));
     chk(pl->linv_exp.alloc(sizeof(int32_t) * (size_t)pl->P * BEOR_TB));
   }
@@ -311,7 +367,15 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, Plan** out) {
   v.linv_sl = pl->linv_sl.as<__nv_bfloat16>();
   v.linv_exp = pl->linv_exp.as<int32_t>();
   v.rows = rows;
-  if (pl->mixed) chk(mixed_maps_create(v, &pl->maps));
+  if (pl->mixed) {
+    chk(mixed_maps_create(v, &pl->maps));
+    int lo = 0, hi = 0;
+    chk(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    pl->prio_hi = hi;
+    chk(cudaStreamCreateWithPriority(&pl->side, cudaStreamNonBlocking, lo));
+    chk(cudaEventCreateWithFlags(&pl->ev_col, cudaEventDisableTiming));
+    chk(cudaEventCreateWithFlags(&pl->ev_rest, cudaEventDisableTiming));
+  }
   chk(cudaEventCreate(&pl->ev0));
   chk(cudaEventCreate(&pl->ev1));
   if (e != cudaSuccess) {
@@ -570,6 +634,7 @@ int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, c
   if (!pl->exec) {
     // first use: run once directly (sets kernel attributes), then capture
     int64_t nl = 0;
+    pl->lookahead = g_lookahead;
     CKC(c0, run_sequence(*pl, st, &nl, false));
     pl->launches = nl;
     CKC(c0, cudaStreamSynchronize(st));
@@ -618,10 +683,9 @@ int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, c
   double cls_ms[kClasses] = {0};
   int64_t cls_n[kClasses] = {0};
   if (pl->prof && ms >= 0.0f) {
-    for (size_t i = 0; i + 1 < pl->pcls.size() + 1 && i + 1 < pl->pev.size(); ++i) {
-      if (i >= pl->pcls.size() || pl->pcls[i] < 0) break;
+    for (size_t i = 0; i < pl->pcls.size() && 2 * i + 1 < pl->pev.size(); ++i) {
       float t = 0.0f;
-      if (cudaEventElapsedTime(&t, pl->pev[i], pl->pev[i + 1]) == cudaSuccess) {
+      if (cudaEventElapsedTime(&t, pl->pev[2 * i], pl->pev[2 * i + 1]) == cudaSuccess) {
         cls_ms[pl->pcls[i]] += t;
         cls_n[pl->pcls[i]] += 1;
       } else {
@@ -719,18 +783,29 @@ int beor_get_dbar(beor_ctx* c, beor_c128* out) {
   return BEOR_OK;
 }
 
-int beor_set_profiling(int on) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  g_profiling = on != 0;
-  // graphs captured with the other setting are rebuilt on their next use
+// graphs captured with another setting are rebuilt on their next use
+static void drop_stale_graphs() {
   for (Plan* p : g_plans) {
-    if (p->prof != g_profiling && p->exec) {
+    if ((p->prof != g_profiling || p->lookahead != g_lookahead) && p->exec) {
       cudaGraphExecDestroy(p->exec);
       cudaGraphDestroy(p->graph);
       p->exec = nullptr;
       p->graph = nullptr;
     }
   }
+}
+
+int beor_set_profiling(int on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_profiling = on != 0;
+  drop_stale_graphs();
+  return BEOR_OK;
+}
+
+int beor_set_lookahead(int on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_lookahead = on != 0;
+  drop_stale_graphs();
   return BEOR_OK;
 }
 

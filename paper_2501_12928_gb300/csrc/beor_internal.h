@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "beor_common.cuh"
 
 namespace beor {
@@ -42,16 +44,34 @@ struct BatchView {
   double* resid;             // [P] refinement residual norm ratio
   Flags* flags;
   // mixed path slice buffers
-  __nv_bfloat16* panel_sl;   // [NPLANE][rows][128], plane = part * NSLICE + slice (part 0 re, 1 im)
-  int32_t* panel_exp;        // [rows]
+  __nv_bfloat16* panel_sl;   // 2 buffers (block step parity) of [NPLANE][rows][128], plane = part * NSLICE + slice
+  int32_t* panel_exp;        // 2 buffers of [rows]
   __nv_bfloat16* linv_sl;    // [NPLANE][P*128][128]
   int32_t* linv_exp;         // [P*128]
   int64_t rows;              // sum of padded dimensions
 };
 
+// Launch with an explicit scheduling priority (0: the stream's own); the
+// attribute is kept by stream capture, so graph nodes carry it too.
+template <typename... Exp, typename... Act>
+static cudaError_t launch_prio(void (*kern)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, int prio,
+                               Act&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = prio;
+  cfg.attrs = at;
+  cfg.numAttrs = prio != 0 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Act>(args)...);
+}
+
 // chol.cu (both precisions)
 cudaError_t launch_prior_init(const BatchView& v, bool mixed, cudaStream_t s);
-cudaError_t launch_diag(const BatchView& v, int k, bool mixed, cudaStream_t s);
+cudaError_t launch_diag(const BatchView& v, int k, bool mixed, cudaStream_t s, int prio = 0);
 cudaError_t launch_panel_f64(const BatchView& v, int k, cudaStream_t s);
 cudaError_t launch_trail_f64(const BatchView& v, int k, cudaStream_t s);
 cudaError_t launch_solve(const BatchView& v, bool mixed, const double2* rhs, double2* out, cudaStream_t s);
@@ -63,9 +83,17 @@ cudaError_t launch_copy_dbar(const BatchView& v, cudaStream_t s);
 struct MixedMaps;  // opaque TMA descriptors of one batch
 cudaError_t mixed_maps_create(const BatchView& v, MixedMaps** out);
 void mixed_maps_destroy(MixedMaps* m);
-cudaError_t launch_slice_panel(const BatchView& v, int k, cudaStream_t s);
-cudaError_t launch_panel_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s);
-cudaError_t launch_trail_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s);
+// Block step k of the mixed factorisation: slicing of the panel column (buffer k % 2),
+// the panel product, and the trailing update, whole or split into the next block
+// column (j = k + 1) and the rest (j >= k + 2) so that step k + 1 can start early.
+// prio: launch priority (0: the stream's).
+enum { TRAIL_ALL = 0, TRAIL_NEXT_COL = 1, TRAIL_REST = 2 };
+cudaError_t mixed_reset_counters(const MixedMaps* m, cudaStream_t s);   // before every evaluation
+int64_t mixed_tiles(const MixedMaps* m, int kind, int k);               // kind 0 next col, 1 rest, 2 panel, 3 all
+cudaError_t launch_slice_panel(const BatchView& v, int k, cudaStream_t s, int prio = 0);
+cudaError_t launch_panel_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s, int prio = 0);
+cudaError_t launch_trail_mixed(const BatchView& v, const MixedMaps* m, int k, int part, cudaStream_t s,
+                               int prio = 0);
 cudaError_t launch_residual(const BatchView& v, cudaStream_t s);      // vec_r = dbar - Sigma x (float64)
 cudaError_t launch_refine_update(const BatchView& v, cudaStream_t s); // x += vec_d; residual norm
 int mixed_supported(int device);

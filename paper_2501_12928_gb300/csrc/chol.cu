@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
   }
 }
 
-cudaError_t launch_diag(const BatchView& v, int k, bool mixed, cudaStream_t s) {
+cudaError_t launch_diag(const BatchView& v, int k, bool mixed, cudaStream_t s, int prio) {
   const size_t smem = sizeof(double2) * (DG_PACK + BEOR_TB);
   static bool init = false;
   if (!init) {
@@ -315,11 +315,8 @@ cudaError_t launch_diag(const BatchView& v, int k, bool mixed, cudaStream_t s) {
     cudaFuncSetAttribute(diag_kernel<float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     init = true;
   }
-  if (mixed)
-    diag_kernel<float4><<<v.P, 512, smem, s>>>(v, k, 1);
-  else
-    diag_kernel<double2><<<v.P, 512, smem, s>>>(v, k, 0);
-  return cudaGetLastError();
+  if (mixed) return launch_prio(diag_kernel<float4>, dim3(v.P), dim3(512), smem, s, prio, v, k, 1);
+  return launch_prio(diag_kernel<double2>, dim3(v.P), dim3(512), smem, s, prio, v, k, 0);
 }
 
 // --------------------------------------------------------------------------

@@ -31,6 +31,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "beor_common.cuh"
@@ -52,15 +53,19 @@ constexpr uint32_t MX_TMEM_COLS = 512;
 constexpr unsigned long long MX_TIMEOUT_NS = 2000000000ull;
 
 enum { MODE_TRAIL = 0, MODE_PANEL = 1 };
+// trailing tiles of block step k: the next block column (j = k + 1) or the rest (j >= k + 2)
+enum { KIND_COL = 0, KIND_REST = 1, KIND_PANEL = 2, KIND_ALL = 3 };
+constexpr int MX_JOBS = 4;               // depth of the producer -> MMA / epilogue job ring
 enum { ERR_TMA_WAIT = 11, ERR_MMA_WAIT = 12, ERR_ACC_WAIT = 13, ERR_EPI_WAIT = 14 };
 
 struct MixedMaps {
-  CUtensorMap panel_a;   // panel slices, box 16 x 128 rows x 10 planes
-  CUtensorMap panel_b;   // panel slices, box 16 x 64 rows x 10 planes
-  CUtensorMap linv_b;    // inverse-diagonal slices, box 16 x 64 rows x 10 planes
-  int64_t* d_prefix = nullptr;   // [max_nt][P+1] tile prefix (trail), then [max_nt][P+1] (panel)
+  CUtensorMap panel_a[2];   // panel slices (two buffers by step parity), box 16 x 128 rows x 10 planes
+  CUtensorMap panel_b[2];   // the same, box 16 x 64 rows x 10 planes
+  CUtensorMap linv_b;       // inverse-diagonal slices, box 16 x 64 rows x 10 planes
+  int64_t* d_prefix = nullptr;   // [4][max_nt][P+1] tile prefix sums (kinds col, rest, panel, all)
+  int* d_counter = nullptr;      // [4][max_nt] dynamic tile counters, zeroed before every evaluation
   int max_nt = 0, P = 0;
-  std::vector<int64_t> h_trail_total, h_panel_total;
+  std::vector<int64_t> h_total[4];
 };
 
 // ---------------------------------------------------------------------------
@@ -202,39 +207,42 @@ __device__ __forceinline__ dfl df_sub_quick(dfl a, dfl b) {
 // tile decoding
 // ---------------------------------------------------------------------------
 struct TileJob {
-  int p, i, j, h;   // problem, output block row, block column (trail: j; panel: k), half
-  bool valid;
+  int p, i, j, h;   // problem (-1: no more work), output block row, block column, column sub-tile
 };
 
-__device__ __forceinline__ TileJob decode_tile(const BatchView& v, const int64_t* prefix, int64_t t, int k,
-                                               int mode) {
-  TileJob jb{0, 0, 0, 0, false};
-  // binary search in prefix[0..P]
+__device__ __forceinline__ void tri_pair(int64_t u, int& a, int& b) {
+  a = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+  while ((int64_t)a * (a + 1) / 2 > u) --a;
+  while ((int64_t)(a + 1) * (a + 2) / 2 <= u) ++a;
+  b = (int)(u - (int64_t)a * (a + 1) / 2);
+}
+
+// Tile t of block step k (kind: next column, rest, or panel); valid = false
+// for problems that failed earlier.
+__device__ __forceinline__ bool decode_tile(const BatchView& v, const int64_t* prefix, int64_t t, int k, int kind,
+                                            TileJob& jb) {
   int lo = 0, hi = v.P;
   while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
+    const int mid = (lo + hi) >> 1;
     if (prefix[mid] <= t) lo = mid; else hi = mid;
   }
   const int p = lo;
   int64_t u = t - prefix[p];
-  const Prob pr = v.prob[p];
-  if (v.status[p] > 0) return jb;
+  if (v.status[p] > 0) return false;
   jb.p = p;
-  jb.h = (int)(u & 1);
-  u >>= 1;
-  if (mode == MODE_TRAIL) {
-    int a = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
-    while ((int64_t)a * (a + 1) / 2 > u) --a;
-    while ((int64_t)(a + 1) * (a + 2) / 2 <= u) ++a;
-    int b = (int)(u - (int64_t)a * (a + 1) / 2);
-    jb.i = k + 1 + a;
-    jb.j = k + 1 + b;
+  jb.h = (int)(u % (BEOR_TB / MX_N));
+  u /= (BEOR_TB / MX_N);
+  if (kind == KIND_REST || kind == KIND_ALL) {
+    const int j0 = kind == KIND_REST ? k + 2 : k + 1;
+    int a, b;
+    tri_pair(u, a, b);
+    jb.i = j0 + a;
+    jb.j = j0 + b;
   } else {
     jb.i = k + 1 + (int)u;
-    jb.j = k;
+    jb.j = kind == KIND_COL ? k + 1 : k;
   }
-  jb.valid = jb.i < pr.nt;
-  return jb;
+  return jb.i < v.prob[p].nt;
 }
 
 // ---------------------------------------------------------------------------
@@ -243,19 +251,24 @@ __device__ __forceinline__ TileJob decode_tile(const BatchView& v, const int64_t
 template <int MODE>
 __global__ void __launch_bounds__(MX_THREADS, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-                      BatchView v, const int64_t* __restrict__ prefix, int64_t ntiles, int k) {
+                      BatchView v, const int64_t* __restrict__ prefix, int64_t ntiles, int k, int kind,
+                      int* __restrict__ counter, const int32_t* __restrict__ pexp) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + MX_STAGES * MX_STAGE_BYTES);
-  // bars[0..2] full, [3..5] empty, [6] acc_full, [7] acc_empty, [8] drain
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 10);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 11);
+  // bars[0..2] full, [3..5] empty, [6] acc_full, [7] acc_empty, [8] drain,
+  // [9..12] job_full, [13..16] job_empty
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 17);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 18);
+  TileJob* jobs = reinterpret_cast<TileJob*>(bars + 20);   // MX_JOBS slots
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (3 + s); };
   const uint32_t acc_full = bar0 + 8u * 6, acc_empty = bar0 + 8u * 7, drain = bar0 + 8u * 8;
+  auto job_full = [&](uint32_t q) { return bar0 + 8u * (9 + q); };
+  auto job_empty = [&](uint32_t q) { return bar0 + 8u * (13 + q); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < MX_STAGES; ++s) {
@@ -265,6 +278,10 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, 32 * MX_EPI_WARPS);
     mbar_init(drain, 1);
+    for (int q = 0; q < MX_JOBS; ++q) {
+      mbar_init(job_full(q), 1);
+      mbar_init(job_empty(q), 1 + MX_EPI_WARPS);   // the MMA thread and one lane per epilogue warp
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     prefetch_map(&map_a);
@@ -282,11 +299,28 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
+    // Tiles are taken from a global counter (CTAs that start late, e.g. after
+    // a concurrent kernel released their SM, simply take fewer) and published
+    // to the MMA and epilogue warps through a ring of MX_JOBS slots.
     if (lane == 0) {
       uint32_t it = 0;
-      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        TileJob jb = decode_tile(v, prefix, t, k, MODE);
-        if (!jb.valid) continue;
+      for (uint32_t n = 0;; ++n) {
+        const uint32_t q = n % MX_JOBS;
+        if (!mbar_wait(job_empty(q), ((n / MX_JOBS) & 1) ^ 1, abort_flag)) {
+          atomicExch(&v.flags->error, ERR_TMA_WAIT);
+          *abort_flag = 1;
+          goto producer_done;
+        }
+        TileJob jb{-1, 0, 0, 0};
+        for (;;) {
+          const int64_t t = atomicAdd(counter, 1);
+          if (t >= ntiles) break;
+          if (decode_tile(v, prefix, t, k, kind, jb)) break;
+          jb.p = -1;
+        }
+        jobs[q] = jb;
+        mbar_arrive(job_full(q));
+        if (jb.p < 0) break;
         const Prob pr = v.prob[jb.p];
         const int a_row = (int)(pr.row_off + (int64_t)jb.i * BEOR_TB);
         const int b_row = MODE == MODE_TRAIL ? (int)(pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N)
@@ -320,9 +354,16 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       uint32_t it = 0, tcount = 0;
-      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        TileJob jb = decode_tile(v, prefix, t, k, MODE);
-        if (!jb.valid) continue;
+      for (uint32_t n = 0;; ++n) {
+        const uint32_t q = n % MX_JOBS;
+        if (!mbar_wait(job_full(q), (n / MX_JOBS) & 1, abort_flag)) {
+          atomicExch(&v.flags->error, ERR_MMA_WAIT);
+          *abort_flag = 1;
+          break;
+        }
+        const TileJob jb = jobs[q];
+        mbar_arrive(job_empty(q));
+        if (jb.p < 0) break;
         if (!mbar_wait(acc_empty, (tcount & 1) ^ 1, abort_flag)) {
           atomicExch(&v.flags->error, ERR_ACC_WAIT);
           *abort_flag = 1;
@@ -388,9 +429,17 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     const int r = lane_base + lane;   // output row within the tile
     const int cbeg = ((warp - 2) >> 2) * (MX_N / 2), cend = cbeg + MX_N / 2;   // this warp's columns
     uint32_t tcount = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      TileJob jb = decode_tile(v, prefix, t, k, MODE);
-      if (!jb.valid) continue;
+    for (uint32_t n = 0;; ++n) {
+      const uint32_t q = n % MX_JOBS;
+      if (!mbar_wait(job_full(q), (n / MX_JOBS) & 1, abort_flag)) {
+        atomicExch(&v.flags->error, ERR_EPI_WAIT);
+        *abort_flag = 1;
+        break;
+      }
+      const TileJob jb = jobs[q];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(job_empty(q));
+      if (jb.p < 0) break;
       if (!mbar_wait(acc_full, tcount & 1, abort_flag)) {
         atomicExch(&v.flags->error, ERR_EPI_WAIT);
         *abort_flag = 1;
@@ -398,8 +447,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       }
       tc_fence_after();
       const Prob pr = v.prob[jb.p];
-      const int e_r = v.panel_exp[pr.row_off + (int64_t)jb.i * BEOR_TB + r];
-      const int32_t* ecol = MODE == MODE_TRAIL ? v.panel_exp + pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N
+      const int e_r = pexp[pr.row_off + (int64_t)jb.i * BEOR_TB + r];
+      const int32_t* ecol = MODE == MODE_TRAIL ? pexp + pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N
                                                : v.linv_exp + (int64_t)jb.p * BEOR_TB + jb.h * MX_N;
       const int out_j = MODE == MODE_TRAIL ? jb.j : k;
       float4* __restrict__ C = reinterpret_cast<float4*>(v.ws) + pr.ws_off + tri_index(jb.i, out_j) * BEOR_TILE_ELEMS +
@@ -468,7 +517,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 // ---------------------------------------------------------------------------
 // slicing of the panel rows: rows of tiles (i, k), i > k, of every problem
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) slice_panel_kernel(BatchView v, int k) {
+__global__ void __launch_bounds__(256)
+    slice_panel_kernel(BatchView v, int k, __nv_bfloat16* __restrict__ panel_sl, int32_t* __restrict__ panel_exp) {
   constexpr int R = 16;                     // rows per block
   __shared__ float4 s[BEOR_TB][R + 1];      // [column][row], padded
   const int p = blockIdx.y;
@@ -494,7 +544,7 @@ __global__ void __launch_bounds__(256) slice_panel_kernel(BatchView v, int k) {
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = mx > 0.0f ? ilogbf(mx) + 1 : -1000;
     const int64_t grow = pr.row_off + (int64_t)i * BEOR_TB + r0 + r;
-    if (lane == 0) v.panel_exp[grow] = e;
+    if (lane == 0) panel_exp[grow] = e;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float4 a = s[lane + 32 * q][r];
@@ -514,7 +564,7 @@ __global__ void __launch_bounds__(256) slice_panel_kernel(BatchView v, int k) {
         dg[0] = (int)X;
 #pragma unroll
         for (int sl = 0; sl < BEOR_NSLICE; ++sl) {
-          __nv_bfloat16* dst = v.panel_sl + ((int64_t)(part * BEOR_NSLICE + sl) * rows + grow) * BEOR_TB + lane + 32 * q;
+          __nv_bfloat16* dst = panel_sl + ((int64_t)(part * BEOR_NSLICE + sl) * rows + grow) * BEOR_TB + lane + 32 * q;
           *dst = __float2bfloat16_rn(ldexpf((float)dg[sl], -8 * sl));
         }
       }
@@ -522,11 +572,16 @@ __global__ void __launch_bounds__(256) slice_panel_kernel(BatchView v, int k) {
   }
 }
 
-cudaError_t launch_slice_panel(const BatchView& v, int k, cudaStream_t s) {
+static __nv_bfloat16* slice_buf(const BatchView& v, int k) {
+  return v.panel_sl + (size_t)(k & 1) * BEOR_NPLANE * v.rows * BEOR_TB;
+}
+static int32_t* exp_buf(const BatchView& v, int k) { return v.panel_exp + (size_t)(k & 1) * v.rows; }
+
+cudaError_t launch_slice_panel(const BatchView& v, int k, cudaStream_t s, int prio) {
   const int nblk = 8 * (v.max_nt - 1 - k);
   if (nblk <= 0) return cudaSuccess;
-  slice_panel_kernel<<<dim3(nblk, v.P), 256, 0, s>>>(v, k);
-  return cudaGetLastError();
+  return launch_prio(slice_panel_kernel, dim3(nblk, v.P), dim3(256), 0, s, prio, v, k, slice_buf(v, k),
+                     exp_buf(v, k));
 }
 
 // ---------------------------------------------------------------------------
@@ -561,14 +616,17 @@ static cudaError_t make_map(CUtensorMap* m, void* base, int64_t rows, int box_ro
 cudaError_t mixed_maps_create(const BatchView& v, MixedMaps** out) {
   *out = nullptr;
   MixedMaps* m = new MixedMaps();
-  cudaError_t e = make_map(&m->panel_a, v.panel_sl, v.rows, MX_M);
-  if (e == cudaSuccess) e = make_map(&m->panel_b, v.panel_sl, v.rows, MX_N);
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = make_map(&m->panel_a[b], slice_buf(v, b), v.rows, MX_M);
+    if (e == cudaSuccess) e = make_map(&m->panel_b[b], slice_buf(v, b), v.rows, MX_N);
+  }
   if (e == cudaSuccess) e = make_map(&m->linv_b, v.linv_sl, (int64_t)v.P * BEOR_TB, MX_N);
   if (e != cudaSuccess) {
     delete m;
     return e;
   }
-  // tile prefix sums per step for both modes
+  // tile prefix sums per step and kind (two 64-column sub-tiles per 128-tile)
   std::vector<Prob> hp(v.P);
   e = cudaMemcpy(hp.data(), v.prob, sizeof(Prob) * v.P, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
@@ -577,25 +635,27 @@ cudaError_t mixed_maps_create(const BatchView& v, MixedMaps** out) {
   }
   m->max_nt = v.max_nt;
   m->P = v.P;
-  std::vector<int64_t> pre((size_t)2 * v.max_nt * (v.P + 1), 0);
-  m->h_trail_total.assign(v.max_nt, 0);
-  m->h_panel_total.assign(v.max_nt, 0);
-  for (int k = 0; k < v.max_nt; ++k) {
-    int64_t* tr = pre.data() + (size_t)k * (v.P + 1);
-    int64_t* pa = pre.data() + (size_t)(v.max_nt + k) * (v.P + 1);
-    for (int p = 0; p < v.P; ++p) {
-      int64_t T = std::max(0, hp[p].nt - k - 1);
-      tr[p + 1] = tr[p] + tri_count((int)T) * 2;
-      pa[p + 1] = pa[p] + T * 2;
+  const int H = BEOR_TB / MX_N;
+  std::vector<int64_t> pre((size_t)4 * v.max_nt * (v.P + 1), 0);
+  for (int kind = 0; kind < 4; ++kind) m->h_total[kind].assign(v.max_nt, 0);
+  for (int kind = 0; kind < 4; ++kind)
+    for (int k = 0; k < v.max_nt; ++k) {
+      int64_t* pk = pre.data() + ((size_t)kind * v.max_nt + k) * (v.P + 1);
+      for (int p = 0; p < v.P; ++p) {
+        const int64_t T = std::max(0, hp[p].nt - k - 1);   // block rows below the diagonal
+        int64_t n = 0;
+        if (kind == KIND_COL || kind == KIND_PANEL) n = T;
+        else if (kind == KIND_REST) n = tri_count((int)std::max<int64_t>(0, T - 1));
+        else n = tri_count((int)T);
+        pk[p + 1] = pk[p] + n * H;
+      }
+      m->h_total[kind][k] = pk[v.P];
     }
-    m->h_trail_total[k] = tr[v.P];
-    m->h_panel_total[k] = pa[v.P];
-  }
   e = cudaMalloc(&m->d_prefix, sizeof(int64_t) * pre.size());
   if (e == cudaSuccess) e = cudaMemcpy(m->d_prefix, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_counter, sizeof(int) * 4 * (size_t)v.max_nt);
   if (e != cudaSuccess) {
-    if (m->d_prefix) cudaFree(m->d_prefix);
-    delete m;
+    mixed_maps_destroy(m);
     return e;
   }
   static bool attr = false;
@@ -611,7 +671,16 @@ cudaError_t mixed_maps_create(const BatchView& v, MixedMaps** out) {
 void mixed_maps_destroy(MixedMaps* m) {
   if (!m) return;
   if (m->d_prefix) cudaFree(m->d_prefix);
+  if (m->d_counter) cudaFree(m->d_counter);
   delete m;
+}
+
+cudaError_t mixed_reset_counters(const MixedMaps* m, cudaStream_t s) {
+  return cudaMemsetAsync(m->d_counter, 0, sizeof(int) * 4 * (size_t)m->max_nt, s);
+}
+
+int64_t mixed_tiles(const MixedMaps* m, int kind, int k) {
+  return k >= 0 && k < m->max_nt ? m->h_total[kind][k] : 0;
 }
 
 static int num_sms() {
@@ -625,22 +694,26 @@ static int num_sms() {
   return n;
 }
 
-cudaError_t launch_panel_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s) {
-  const int64_t nt = m->h_panel_total[k];
+static cudaError_t launch_gemm(const BatchView& v, const MixedMaps* m, int k, int kind, cudaStream_t s, int prio) {
+  const int64_t nt = m->h_total[kind][k];
   if (nt <= 0) return cudaSuccess;
   const int grid = (int)std::min<int64_t>(nt, num_sms());
-  const int64_t* pre = m->d_prefix + (size_t)(m->max_nt + k) * (m->P + 1);
-  slice_gemm_kernel<MODE_PANEL><<<grid, MX_THREADS, MX_SMEM, s>>>(m->panel_a, m->linv_b, v, pre, nt, k);
-  return cudaGetLastError();
+  const int64_t* pre = m->d_prefix + ((size_t)kind * m->max_nt + k) * (m->P + 1);
+  int* ctr = m->d_counter + (size_t)kind * m->max_nt + k;
+  if (kind == KIND_PANEL)
+    return launch_prio(slice_gemm_kernel<MODE_PANEL>, dim3(grid), dim3(MX_THREADS), (size_t)MX_SMEM, s, prio,
+                       m->panel_a[k & 1], m->linv_b, v, pre, nt, k, kind, ctr, (const int32_t*)exp_buf(v, k));
+  return launch_prio(slice_gemm_kernel<MODE_TRAIL>, dim3(grid), dim3(MX_THREADS), (size_t)MX_SMEM, s, prio,
+                     m->panel_a[k & 1], m->panel_b[k & 1], v, pre, nt, k, kind, ctr, (const int32_t*)exp_buf(v, k));
 }
 
-cudaError_t launch_trail_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s) {
-  const int64_t nt = m->h_trail_total[k];
-  if (nt <= 0) return cudaSuccess;
-  const int grid = (int)std::min<int64_t>(nt, num_sms());
-  const int64_t* pre = m->d_prefix + (size_t)k * (m->P + 1);
-  slice_gemm_kernel<MODE_TRAIL><<<grid, MX_THREADS, MX_SMEM, s>>>(m->panel_a, m->panel_b, v, pre, nt, k);
-  return cudaGetLastError();
+cudaError_t launch_panel_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s, int prio) {
+  return launch_gemm(v, m, k, KIND_PANEL, s, prio);
+}
+
+cudaError_t launch_trail_mixed(const BatchView& v, const MixedMaps* m, int k, int part, cudaStream_t s, int prio) {
+  const int kind = part == TRAIL_NEXT_COL ? KIND_COL : part == TRAIL_REST ? KIND_REST : KIND_ALL;
+  return launch_gemm(v, m, k, kind, s, prio);
 }
 
 // ---------------------------------------------------------------------------

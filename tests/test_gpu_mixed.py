@@ -90,3 +90,54 @@ def test_mixed_and_fp64_C1_full_size(P):
     gf, sf = lf.lnl(ph)
     assert np.all(sf == 0)
     assert np.all(np.abs(gf - np.array([r["lnl"] for r in refs])) <= 1e-10 * np.abs([r["lnl"] for r in refs]))
+
+
+def _uneven_batch(P):
+    likes, refs, phs = [], [], []
+    for nvis, n, nk in ((700, 640, 4), (400, 383, 3), (1300, 1100, 5)):
+        p = random_problem(nvis, n, nk, seed=n + 7)
+        lk = P.Likelihood("mixed")
+        lk.set_T(p["T"], p["kbin"], nk, 2.0)
+        lk.set_data(p["d"], p["noise_var"])
+        lk.precompute()
+        ph = np.random.default_rng(n + 3).uniform(-2, 2, (3, nk))
+        M = O.herm_dense(p["T"], p["noise_var"])
+        db = O.dbar_dense(p["T"], p["noise_var"], p["d"])
+        refs.append([O.evaluate(M, db, p["kbin"], q, 2.0)["lnl"] for q in ph])
+        likes.append(lk)
+        phs.append(ph)
+    return likes, phs, refs
+
+
+def test_lookahead_schedule_is_bitwise_in_order(P):
+    """The look-ahead schedule (split trailing update on two streams, dynamic
+    tile order) applies the same operations to every tile as the in-order
+    schedule: the Cholesky factors agree bit for bit, with and without
+    profiling events, on a batch of uneven sizes (5, 3 and 9 block steps).
+    lnL agrees to rounding (the float64 refinement residual sums tiles with
+    atomics, in no fixed order)."""
+    likes, phs, refs = _uneven_batch(P)
+    runs = {}
+    try:
+        for la in (True, False):
+            for prof in (False, True):
+                P.set_lookahead(la)
+                P.set_profiling(prof)
+                for _ in range(2):   # first call runs directly, the second replays the graph
+                    outs, sts = P.lnl_multi(likes, phs)
+                    assert all(np.all(s == 0) for s in sts)
+                    facs = [lk.factor(b) for lk in likes for b in (0, 2)]
+                    runs.setdefault((la, prof), []).append((np.concatenate(outs), facs))
+    finally:
+        P.set_lookahead(True)
+        P.set_profiling(False)
+    base, base_f = runs[(False, False)][0]
+    for key, vals in runs.items():
+        for v, f in vals:
+            for a, b in zip(f, base_f):
+                assert np.array_equal(a, b), key
+            assert np.allclose(v, base, rtol=1e-13, atol=0), (key, v - base)
+    err = np.abs(base - np.concatenate(refs))
+    assert err.max() <= ATOL_LNL, err
+    st = likes[0].stats()
+    assert st["n_class"]["trail"] > 0 and st["ms_class"]["trail"] > 0
