@@ -166,7 +166,20 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Pins four registers written by tcgen05.ld after the wait that completes the
+// load, so that no use of them is scheduled before it.
+__device__ __forceinline__ void reg_fence4(float* v) {
+  asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]));
+}
 
 // Shared-memory matrix descriptor: K-major operand, 32-byte swizzle, 8-row
 // groups 256 bytes apart (SBO), leading offset unused (K of one MMA fits the
@@ -440,12 +453,6 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(job_empty(q));
       if (jb.p < 0) break;
-      if (!mbar_wait(acc_full, tcount & 1, abort_flag)) {
-        atomicExch(&v.flags->error, ERR_EPI_WAIT);
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
       const Prob pr = v.prob[jb.p];
       const int e_r = pexp[pr.row_off + (int64_t)jb.i * BEOR_TB + r];
       const int32_t* ecol = MODE == MODE_TRAIL ? pexp + pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N
@@ -454,39 +461,71 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       float4* __restrict__ C = reinterpret_cast<float4*>(v.ws) + pr.ws_off + tri_index(jb.i, out_j) * BEOR_TILE_ELEMS +
                   (int64_t)(jb.h * MX_N) * BEOR_TB + r;
       const uint32_t trow = tmem + ((uint32_t)lane_base << 16);
-      constexpr int EC = 8;   // columns per epilogue chunk
-      float4 cv[EC], cn[EC];
+      constexpr int NC = MX_N / 2;   // this warp's columns
+      constexpr int EC = 4;          // columns per chunk
+      // the first working-matrix columns do not depend on the product: load them before it is done
+      float4 cv[EC];
       if (MODE == MODE_TRAIL) {
 #pragma unroll
         for (int q = 0; q < EC; ++q) cv[q] = __ldcs(C + (int64_t)(cbeg + q) * BEOR_TB);
       }
-#pragma unroll 1
-      for (int c0 = cbeg; c0 < cend; c0 += EC) {
-        // prefetch the next chunk of the working matrix while this one is processed
-        if (MODE == MODE_TRAIL && c0 + EC < cend) {
+      if (!mbar_wait(acc_full, tcount & 1, abort_flag)) {
+        atomicExch(&v.flags->error, ERR_EPI_WAIT);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      // Phase 1: the four level accumulators of each output, summed to a
+      // double-float, move from tensor memory to registers; then tensor
+      // memory is released, and the next tile's products run during phase 2.
+      float prh[NC], prl[NC], pih[NC], pil[NC];
 #pragma unroll
-          for (int q = 0; q < EC; ++q) cn[q] = __ldcs(C + (int64_t)(c0 + EC + q) * BEOR_TB);
-        }
-        float lr[4][EC], li[4][EC];
+      for (int c0 = 0; c0 < NC; c0 += 4) {
+        float lr[4][4], li[4][4];
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
-          tmem_ld8(trow + (uint32_t)(l * MX_N + c0), lr[l]);
-          tmem_ld8(trow + 256u + (uint32_t)(l * MX_N + c0), li[l]);
+          tmem_ld4(trow + (uint32_t)(l * MX_N + cbeg + c0), lr[l]);
+          tmem_ld4(trow + 256u + (uint32_t)(l * MX_N + cbeg + c0), li[l]);
         }
         tmem_ld_wait();
 #pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          reg_fence4(lr[l]);
+          reg_fence4(li[l]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const dfl vr = levels_sum(lr[0][q], lr[1][q], lr[2][q], lr[3][q]);
+          const dfl vi = levels_sum(li[0][q], li[1][q], li[2][q], li[3][q]);
+          prh[c0 + q] = vr.hi;
+          prl[c0 + q] = vr.lo;
+          pih[c0 + q] = vi.hi;
+          pil[c0 + q] = vi.lo;
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(acc_empty);
+      // Phase 2: scale by 2^(e_r + e_c - 14) and subtract from (trail) or
+      // store into (panel) the working matrix.
+#pragma unroll
+      for (int c0 = 0; c0 < NC; c0 += EC) {
+        float4 cn[EC];
+        if (MODE == MODE_TRAIL && c0 + EC < NC) {
+#pragma unroll
+          for (int q = 0; q < EC; ++q) cn[q] = __ldcs(C + (int64_t)(cbeg + c0 + EC + q) * BEOR_TB);
+        }
+#pragma unroll
         for (int q = 0; q < EC; ++q) {
-          const int ec = __ldg(ecol + c0 + q);
+          const int c = cbeg + c0 + q;
+          const int ec = __ldg(ecol + c);
           int ex = e_r + ec - 14;
           if (e_r <= -1000 || ec <= -1000) ex = 0;
           ex = max(-250, min(250, ex));
           const int e1 = ex >> 1, e2 = ex - e1;   // two exact power-of-two factors
           const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
-          dfl vr = levels_sum(lr[0][q], lr[1][q], lr[2][q], lr[3][q]);
-          dfl vi = levels_sum(li[0][q], li[1][q], li[2][q], li[3][q]);
-          vr.hi = vr.hi * s1 * s2; vr.lo = vr.lo * s1 * s2;
-          vi.hi = vi.hi * s1 * s2; vi.lo = vi.lo * s1 * s2;
-          float4* cp = C + (int64_t)(c0 + q) * BEOR_TB;
+          const dfl vr{prh[c0 + q] * s1 * s2, prl[c0 + q] * s1 * s2};
+          const dfl vi{pih[c0 + q] * s1 * s2, pil[c0 + q] * s1 * s2};
+          float4* cp = C + (int64_t)c * BEOR_TB;
           if (MODE == MODE_TRAIL) {
             const float4 w = cv[q];
             const dfl wr = df_sub_quick(dfl{w.x, w.y}, vr);
@@ -501,8 +540,6 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           for (int q = 0; q < EC; ++q) cv[q] = cn[q];
         }
       }
-      tc_fence_before();
-      mbar_arrive(acc_empty);
       ++tcount;
     }
   }
