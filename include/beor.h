@@ -36,9 +36,11 @@
  *  - Complex numbers are beor_c128 {re, im} pairs (same layout as
  *    std::complex<double> / numpy complex128); matrices are row-major.
  *  - Per-point status: 0 = ok; j > 0 = Sigma not positive definite at
- *    1-based column j (lnL = -inf); -1 = iterative refinement of the solve
- *    did not converge (last correction above 1e-4 of the solution; lnL
- *    still returned).
+ *    1-based column j (lnL = -inf); -1 = the mixed-precision result may be
+ *    outside its tolerance (lnL still returned): for beor_lnl /
+ *    beor_lnl_multi, the estimated error of the residual-corrected
+ *    quadratic form is above 1e-2; for beor_posterior_mean, the last
+ *    iterative-refinement correction is above 1e-4 of the solution.
  */
 #ifndef BEOR_H
 #define BEOR_H
@@ -106,7 +108,11 @@ int beor_precompute(beor_ctx *ctx, void *stream);
 /* lnL for B prior points.  phi: B x n_k float64, row-major, log10 power
  * amplitudes (host or device).  lnl_out: B float64, status_out: B int32
  * (host or device).  The whole batch is factorised together; the call
- * returns after the results are written. */
+ * returns after the results are written.
+ * Mixed precision: the quadratic form q = dbar^H Sigma^-1 dbar is evaluated
+ * from the first solution x~ of the approximate factor L~ and one float64
+ * residual r = dbar - Sigma x~ as q = dbar^H x~ + x~^H r + |L~^-1 r|^2
+ * (exact up to the factor error of the last, second-order term). */
 int beor_lnl(beor_ctx *ctx, const double *phi, int B, double *lnl_out, int32_t *status_out,
              void *stream);
 
@@ -136,8 +142,10 @@ int beor_get_dbar(beor_ctx *ctx, beor_c128 *dbar_out);
  * when profiling is on (beor_set_profiling); ms_last is -1 on the call that
  * captures a batch's graph. */
 typedef struct {
-  int refine_iters_max;     /* refinement steps taken */
-  double resid_rel_max;     /* largest last refinement correction ||d|| / ||x|| */
+  int refine_iters_max;     /* refinement steps taken (posterior mean; 0 for lnL calls) */
+  double resid_rel_max;     /* posterior mean: largest last refinement correction ||d|| / ||x||;
+                               mixed lnL: largest sqrt(|L~^-1 r|^2 / q), the relative error of
+                               x~ in the Sigma norm */
   double ms_last;           /* device time of the last batched evaluation */
   int64_t kernel_launches;  /* kernels launched by the last batched evaluation */
   double ms_class[8];

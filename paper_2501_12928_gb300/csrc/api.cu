@@ -119,6 +119,7 @@ struct Plan {
   int64_t launches = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool prof = false;
+  bool refine_x = false;            // mixed: refine the solution (posterior mean) rather than correct q
   bool lookahead = true;            // schedule of the mixed factorisation captured in the graph
   int prio_hi = 0;                  // greatest stream priority of the device
   std::vector<cudaEvent_t> pev;     // boundary events (profiling)
@@ -253,15 +254,23 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
   }
   RUN(KC_SOLVE, launch_solve(v, pl.mixed, v.vec_b, v.vec_x, s));
   L += solve_launch_count(pl.max_nt);
-  if (pl.mixed) {
+  const bool corr = pl.mixed && !pl.refine_x;
+  if (pl.mixed && pl.refine_x) {
+    // the solution itself is wanted (posterior mean): float64 iterative refinement
     for (int it = 0; it < kRefineIters; ++it) {
       RUN(KC_REFINE, launch_residual(v, s));
       RUN(KC_SOLVE, launch_solve(v, true, v.vec_r, v.vec_d, s));
       RUN(KC_REFINE, launch_refine_update(v, s));
       L += 4 + solve_launch_count(pl.max_nt);
     }
+  } else if (corr) {
+    // lnL only: one float64 residual r = dbar - Sigma x~ and y = L~^-1 r
+    // correct the quadratic form (see lnl_kernel)
+    RUN(KC_REFINE, launch_residual(v, s));
+    RUN(KC_SOLVE, launch_solve_fwd(v, true, v.vec_r, s));
+    L += 3 + pl.max_nt;
   }
-  RUN(KC_LNL, launch_lnl(v, s));
+  RUN(KC_LNL, launch_lnl(v, s, corr ? 1 : 0));
   L += 1;
 #undef RUN
 #undef RUN_ON
@@ -269,8 +278,9 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
   return cudaSuccess;
 }
 
-int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, Plan** out) {
+int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, Plan** out) {
   Plan* pl = new Plan();
+  pl->refine_x = need_x;
   pl->device = ctxs[0]->device;
   pl->mixed = ctxs[0]->precision == BEOR_PREC_MIXED;
   int64_t ws_elems = 0, dinv_elems = 0, rows = 0;
@@ -386,9 +396,9 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, Plan** out) {
   return BEOR_OK;
 }
 
-Plan* find_plan(beor_ctx* const* ctxs, int nsets, const int* Bs) {
+Plan* find_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x) {
   for (Plan* p : g_plans) {
-    if ((int)p->ctxs.size() != nsets) continue;
+    if ((int)p->ctxs.size() != nsets || p->refine_x != need_x) continue;
     bool same = true;
     for (int s = 0; s < nsets && same; ++s) same = p->ctxs[s] == ctxs[s] && p->Bs[s] == Bs[s];
     if (same) return p;
@@ -602,8 +612,8 @@ int beor_precompute(beor_ctx* c, void* stream) {
   return BEOR_OK;
 }
 
-int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, const int* B,
-                   double* const* lnl_out, int32_t* const* status_out, void* stream) {
+static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const* phi, const int* B,
+                          double* const* lnl_out, int32_t* const* status_out, void* stream, bool need_x) {
   if (!ctxs || nsets <= 0 || !phi || !B) return BEOR_EINVAL;
   for (int s = 0; s < nsets; ++s) {
     int r = check_ready(ctxs[s]);
@@ -616,9 +626,10 @@ int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, c
   cudaSetDevice(c0->device);
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(g_mu);
-  Plan* pl = find_plan(ctxs, nsets, B);
+  need_x = need_x && ctxs[0]->precision == BEOR_PREC_MIXED;
+  Plan* pl = find_plan(ctxs, nsets, B, need_x);
   if (!pl) {
-    int r = build_plan(ctxs, nsets, B, &pl);
+    int r = build_plan(ctxs, nsets, B, need_x, &pl);
     if (r) return r;
     g_plans.push_back(pl);
   }
@@ -700,7 +711,7 @@ int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, c
     beor_ctx* c = ctxs[s];
     c->stats.ms_last = ms;
     c->stats.kernel_launches = pl->launches;
-    c->stats.refine_iters_max = pl->mixed ? kRefineIters : 0;
+    c->stats.refine_iters_max = pl->mixed && pl->refine_x ? kRefineIters : 0;
     double mx = 0.0;
     for (int b = 0; b < B[s]; ++b) mx = std::max(mx, resid[pl->first[s] + b]);
     c->stats.resid_rel_max = mx;
@@ -714,6 +725,11 @@ int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, c
   return BEOR_OK;
 }
 
+int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, const int* B,
+                   double* const* lnl_out, int32_t* const* status_out, void* stream) {
+  return lnl_multi_impl(ctxs, nsets, phi, B, lnl_out, status_out, stream, false);
+}
+
 int beor_lnl(beor_ctx* c, const double* phi, int B, double* lnl_out, int32_t* status_out, void* stream) {
   return beor_lnl_multi(&c, 1, &phi, &B, &lnl_out, &status_out, stream);
 }
@@ -725,7 +741,7 @@ int beor_posterior_mean(beor_ctx* c, const double* phi, beor_c128* abar_out, int
   int B = 1;
   double* lo = &l;
   int32_t* so = &st;
-  int r = beor_lnl_multi(&c, 1, &phi, &B, &lo, &so, stream);
+  int r = lnl_multi_impl(&c, 1, &phi, &B, &lo, &so, stream, true);
   if (r) return r;
   Plan* pl = c->last_plan;
   CKC(c, from_device(abar_out, pl->view.vec_x + pl->h_prob[c->last_first].row_off, sizeof(double2) * c->n,

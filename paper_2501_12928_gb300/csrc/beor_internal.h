@@ -76,7 +76,8 @@ cudaError_t launch_panel_f64(const BatchView& v, int k, cudaStream_t s);
 cudaError_t launch_trail_f64(const BatchView& v, int k, cudaStream_t s);
 cudaError_t launch_solve(const BatchView& v, bool mixed, const double2* rhs, double2* out, cudaStream_t s);
 int solve_launch_count(int max_nt);
-cudaError_t launch_lnl(const BatchView& v, cudaStream_t s);
+cudaError_t launch_lnl(const BatchView& v, cudaStream_t s, int corr);   // corr: residual-corrected q
+cudaError_t launch_solve_fwd(const BatchView& v, bool mixed, const double2* rhs, cudaStream_t s);   // vec_y = L^-1 rhs
 cudaError_t launch_copy_dbar(const BatchView& v, cudaStream_t s);
 
 // mixed.cu

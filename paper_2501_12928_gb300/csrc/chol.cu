@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(256) bwd_step_kernel(BatchView v, int k, doubl
 constexpr size_t kBwdSmem = 16 * 64 * 129 + sizeof(CAcc) * 256;
 
 template <typename WS>
-static cudaError_t solve_impl(const BatchView& v, const double2* rhs, double2* out, cudaStream_t s) {
+static cudaError_t solve_impl(const BatchView& v, const double2* rhs, double2* out, bool back, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(bwd_step_kernel<WS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
@@ -684,6 +684,7 @@ static cudaError_t solve_impl(const BatchView& v, const double2* rhs, double2* o
   const int nt = v.max_nt;
   fwd_step_kernel<WS><<<dim3(nt, v.P), 256, 0, s>>>(v, -1, rhs);
   for (int k = 0; k + 1 < nt; ++k) fwd_step_kernel<WS><<<dim3(nt - k - 1, v.P), 256, 0, s>>>(v, k, rhs);
+  if (!back) return cudaGetLastError();
   bwd_step_kernel<WS><<<dim3(nt, v.P), 256, kBwdSmem, s>>>(v, nt, out);
   for (int k = nt - 1; k >= 1; --k) {
     // problems whose last block is k-1 (nt_p == k) start here
@@ -693,7 +694,11 @@ static cudaError_t solve_impl(const BatchView& v, const double2* rhs, double2* o
 }
 
 cudaError_t launch_solve(const BatchView& v, bool mixed, const double2* rhs, double2* out, cudaStream_t s) {
-  return mixed ? solve_impl<float4>(v, rhs, out, s) : solve_impl<double2>(v, rhs, out, s);
+  return mixed ? solve_impl<float4>(v, rhs, out, true, s) : solve_impl<double2>(v, rhs, out, true, s);
+}
+
+cudaError_t launch_solve_fwd(const BatchView& v, bool mixed, const double2* rhs, cudaStream_t s) {
+  return mixed ? solve_impl<float4>(v, rhs, nullptr, false, s) : solve_impl<double2>(v, rhs, nullptr, false, s);
 }
 
 int solve_launch_count(int max_nt) { return 2 * max_nt; }
@@ -717,18 +722,40 @@ cudaError_t launch_copy_dbar(const BatchView& v, cudaStream_t s) {
 // --------------------------------------------------------------------------
 // lnL = -1/2 log|Phi| - 1/2 log|Sigma| + 1/2 Re(dbar^H x)
 // --------------------------------------------------------------------------
-__global__ void lnl_kernel(BatchView v) {
+// lnL = -1/2 log|Phi| - 1/2 log|Sigma| + 1/2 q (Eq. for the marginal
+// likelihood of the power spectrum).  corr = 0: q = Re(dbar^H x), x the
+// (refined) solution.  corr = 1: q from the first solution x~ of the
+// approximate factor, corrected with the float64 residual r = dbar - Sigma x~
+// (vec_r) and y = L~^-1 r (vec_y):
+//   q = dbar^H x~ + x~^H r + r^H Sigma^-1 r,  r^H Sigma^-1 r ~ |y|^2,
+// exact but for the last term's factor error, about eta |y|^2 with
+// eta ~ sqrt(|y|^2 / q) the relative error of x~ in the Sigma norm.
+__global__ void lnl_kernel(BatchView v, int corr) {
   const int p = blockIdx.x;
   const Prob pr = v.prob[p];
   const SetDesc sd = v.sets[pr.set];
   __shared__ double red[33];
-  double acc = 0.0;
+  double acc = 0.0, t = 0.0;
   for (int j = threadIdx.x; j < pr.n; j += blockDim.x) {
     double2 d = sd.dbar[j], x = v.vec_x[pr.row_off + j];
     acc += d.x * x.x + d.y * x.y;
+    if (corr) {
+      const double2 r = v.vec_r[pr.row_off + j], y = v.vec_y[pr.row_off + j];
+      acc += x.x * r.x + x.y * r.y;
+      t += y.x * y.x + y.y * y.y;
+    }
   }
   double q = block_sum(acc, red);
+  __syncthreads();
+  if (corr) t = block_sum(t, red);
   if (threadIdx.x == 0) {
+    if (corr) {
+      q += t;
+      const double eta = q > 0.0 ? sqrt(t / q) : INFINITY;
+      v.resid[p] = eta;
+      // estimated remaining error of q above 1e-2 (5e-3 in lnL): flag
+      if (v.status[p] == 0 && !(eta * t <= 1e-2)) v.status[p] = -1;
+    }
     v.q[p] = q;
     if (v.status[p] > 0)
       v.lnl[p] = -INFINITY;
@@ -737,8 +764,8 @@ __global__ void lnl_kernel(BatchView v) {
   }
 }
 
-cudaError_t launch_lnl(const BatchView& v, cudaStream_t s) {
-  lnl_kernel<<<v.P, 256, 0, s>>>(v);
+cudaError_t launch_lnl(const BatchView& v, cudaStream_t s, int corr) {
+  lnl_kernel<<<v.P, 256, 0, s>>>(v, corr);
   return cudaGetLastError();
 }
 

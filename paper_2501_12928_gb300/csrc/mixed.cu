@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     // ---------------- epilogue (warps 2..9) ----------------
     const int lane_base = 32 * (warp & 3);
     const int r = lane_base + lane;   // output row within the tile
-    const int cbeg = ((warp - 2) >> 2) * (MX_N / 2), cend = cbeg + MX_N / 2;   // this warp's columns
+    const int cbeg = ((warp - 2) >> 2) * (MX_N / 2);   // first of this warp's 32 columns
     uint32_t tcount = 0;
     for (uint32_t n = 0;; ++n) {
       const uint32_t q = n % MX_JOBS;
