@@ -87,7 +87,7 @@ struct beor_ctx {
   DevBuf d, w;
   // precompute
   bool have_pre = false;
-  DevBuf M, dbar, Mdf;
+  DevBuf M, dbar, Mdf, Mf, Mft;
   // bookkeeping
   beor_stats stats{};
   Plan* last_plan = nullptr;
@@ -111,6 +111,8 @@ struct Plan {
   std::vector<SetDesc> h_sets;
   std::vector<int> first;   // first problem index of each set
   DevBuf d_prob, d_sets, ws, dinv, phi_inv, vecs, scal, flags, phis, panel_sl, panel_exp, linv_sl, linv_exp;
+  DevBuf xtr, rwork;                // float32-pipe residual: x triples, work items
+  int n_rwork = 0;
   std::vector<int64_t> phi_off;
   BatchView view{};
   MixedMaps* maps = nullptr;
@@ -261,14 +263,14 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
       RUN(KC_REFINE, launch_residual(v, s));
       RUN(KC_SOLVE, launch_solve(v, true, v.vec_r, v.vec_d, s));
       RUN(KC_REFINE, launch_refine_update(v, s));
-      L += 4 + solve_launch_count(pl.max_nt);
+      L += 5 + solve_launch_count(pl.max_nt);
     }
   } else if (corr) {
     // lnL only: one float64 residual r = dbar - Sigma x~ and y = L~^-1 r
     // correct the quadratic form (see lnl_kernel)
     RUN(KC_REFINE, launch_residual(v, s));
     RUN(KC_SOLVE, launch_solve_fwd(v, true, v.vec_r, s));
-    L += 3 + pl.max_nt;
+    L += 4 + pl.max_nt;
   }
   RUN(KC_LNL, launch_lnl(v, s, corr ? 1 : 0));
   L += 1;
@@ -297,6 +299,8 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, Pla
     sd.lssm_prior_var = c->lssm_prior_var;
     sd.M = c->M.as<double2>();
     sd.Mdf = c->Mdf.as<float4>();
+    sd.Mf = c->Mf.as<float4>();
+    sd.Mft = c->Mft.as<float2>();
     sd.dbar = c->dbar.as<double2>();
     sd.kbin = c->kbin.as<int32_t>();
     pl->phi_off.push_back(phi_total);
@@ -339,6 +343,19 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, Pla
     chk(pl->panel_exp.alloc(sizeof(int32_t) * 2 * (size_t)rows));
     chk(pl->linv_sl.alloc(sizeof(__nv_bfloat16) * (size_t)BEOR_NPLANE * pl->P * BEOR_TB * BEOR_TB));
     chk(pl->linv_exp.alloc(sizeof(int32_t) * (size_t)pl->P * BEOR_TB));
+    chk(pl->xtr.alloc(sizeof(float) * 6 * (size_t)rows));
+    // residual work items: row block x 16 block columns x 16 problems
+    std::vector<RWork> wk;
+    for (int s = 0; s < nsets; ++s) {
+      const int nt = ctxs[s]->nt;
+      for (int I = 0; I < nt; ++I)
+        for (int j0 = 0; j0 < nt; j0 += 16)
+          for (int g = 0; g < Bs[s]; g += 16)
+            wk.push_back(RWork{s, I, j0, std::min(nt, j0 + 16), pl->first[s] + g, std::min(16, Bs[s] - g)});
+    }
+    pl->n_rwork = (int)wk.size();
+    chk(pl->rwork.alloc(sizeof(RWork) * wk.size()));
+    if (e == cudaSuccess) chk(cudaMemcpy(pl->rwork.p, wk.data(), sizeof(RWork) * wk.size(), cudaMemcpyHostToDevice));
   }
   if (e != cudaSuccess) {
     delete pl;
@@ -376,6 +393,9 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, Pla
   v.panel_exp = pl->panel_exp.as<int32_t>();
   v.linv_sl = pl->linv_sl.as<__nv_bfloat16>();
   v.linv_exp = pl->linv_exp.as<int32_t>();
+  v.xtr = pl->xtr.as<float>();
+  v.rwork = pl->rwork.as<RWork>();
+  v.n_rwork = pl->n_rwork;
   v.rows = rows;
   if (pl->mixed) {
     chk(mixed_maps_create(v, &pl->maps));
@@ -606,6 +626,10 @@ int beor_precompute(beor_ctx* c, void* stream) {
     const int64_t ne = tri_count(c->nt) * BEOR_TILE_ELEMS;
     CKC(c, c->Mdf.alloc(sizeof(float4) * (size_t)ne));
     CKC(c, split_double_float(c->M.as<double2>(), ne, c->Mdf.as<float4>(), s));
+    const int64_t nf = (int64_t)c->nt * c->nt * BEOR_TILE_ELEMS;
+    CKC(c, c->Mf.alloc(sizeof(float4) * (size_t)nf));
+    CKC(c, c->Mft.alloc(sizeof(float2) * (size_t)nf));
+    CKC(c, split_full_triple(c->M.as<double2>(), c->n, c->nt, c->Mf.as<float4>(), c->Mft.as<float2>(), s));
   }
   CKC(c, cudaStreamSynchronize(s));
   c->have_pre = true;

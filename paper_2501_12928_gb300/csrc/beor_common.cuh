@@ -41,9 +41,18 @@ struct SetDesc {
   double lssm_prior_var;
   const double2* M;       // packed tiles (float64), lower
   const float4* Mdf;      // the same as double-float pairs (mixed contexts), or null
+  const float4* Mf;       // mixed: all nt x nt tiles (upper ones as conjugate transposes), each
+                          // element split exactly m = hi + lo + t: {re hi, re lo, im hi, im lo}
+  const float2* Mft;      // ... and {re t, im t}
   const double2* dbar;    // Np
   const int32_t* kbin;    // n
   const double* phi;      // B x n_k (device staging)
+};
+
+// One CTA of the float64-accurate residual: row block I of set `set`
+// against block columns [j0, j1), for problems p0 .. p0 + nb - 1.
+struct RWork {
+  int set, I, j0, j1, p0, nb;
 };
 
 // Bounds of the per-call device state shared by kernels.

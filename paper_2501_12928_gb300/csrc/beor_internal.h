@@ -12,6 +12,9 @@ namespace beor {
 
 // precompute.cu
 cudaError_t split_double_float(const double2* M, int64_t n, float4* out, cudaStream_t s);
+// Full nt x nt tile square of the packed lower M (n x n, padding zero), each
+// element split exactly into three floats per component.
+cudaError_t split_full_triple(const double2* M, int n, int nt, float4* hl, float2* t, cudaStream_t s);
 cudaError_t precompute_dense(const double2* T, int64_t n_vis, int n, int64_t ld, const double* w,
                              const double2* d, int nt, double2* Mt, double2* dbar, cudaStream_t s);
 cudaError_t precompute_factored(const double2* A, const double2* W, int nf, int64_t ntb, int ncells,
@@ -48,6 +51,10 @@ struct BatchView {
   int32_t* panel_exp;        // 2 buffers of [rows]
   __nv_bfloat16* linv_sl;    // [NPLANE][P*128][128]
   int32_t* linv_exp;         // [P*128]
+  // float64-accurate residual on the float32 pipe (mixed path)
+  float* xtr;                // [rows][6]: x re (hi, lo, t), im (hi, lo, t)
+  const RWork* rwork;        // CTA work items
+  int n_rwork;
   int64_t rows;              // sum of padded dimensions
 };
 

@@ -768,63 +768,106 @@ __global__ void resid_init_kernel(BatchView v) {
   }
 }
 
-// One CTA per (problem, lower tile of M) -- problems fastest, so the problems
-// of one instrument share each M tile through L2: r_I -= M_IJ x_J and, off
-// the diagonal, r_J -= M_IJ^H x_I, accumulated with float64 atomics.
-__global__ void __launch_bounds__(128) resid_tile_kernel(BatchView v) {
-  __shared__ double2 xj[BEOR_TB], xi[BEOR_TB];
-  const int p = blockIdx.x;
+// x split exactly into three floats per component (hi, lo, t), for the
+// float32-pipe residual below.
+__global__ void xsplit_kernel(BatchView v) {
+  const int p = blockIdx.y;
   const Prob pr = v.prob[p];
-  const SetDesc sd = v.sets[pr.set];
-  const int64_t t = blockIdx.y;
-  if (t >= tri_count(pr.nt) || v.status[p] > 0) return;
-  int I, J;
-  {
-    int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-    while ((int64_t)a * (a + 1) / 2 > t) --a;
-    while ((int64_t)(a + 1) * (a + 2) / 2 <= t) ++a;
-    I = a;
-    J = (int)(t - (int64_t)a * (a + 1) / 2);
+  const int np = pr.nt * BEOR_TB;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += gridDim.x * blockDim.x) {
+    const double2 x = v.vec_x[pr.row_off + j];
+    float* o = v.xtr + (pr.row_off + j) * 6;
+    const float rh = (float)x.x, ih = (float)x.y;
+    const double rd = x.x - (double)rh, id = x.y - (double)ih;
+    const float rl = (float)rd, il = (float)id;
+    o[0] = rh;
+    o[1] = rl;
+    o[2] = (float)(rd - (double)rl);
+    o[3] = ih;
+    o[4] = il;
+    o[5] = (float)(id - (double)il);
   }
-  const double2* Mt = sd.M + t * BEOR_TILE_ELEMS;
-  const double2* x = v.vec_x + pr.row_off;
-  double2* r = v.vec_r + pr.row_off;
-  const int tid = threadIdx.x;
-  xj[tid] = x[J * BEOR_TB + tid];
-  xi[tid] = x[I * BEOR_TB + tid];
-  __syncthreads();
-  // rows of block I
-  double sr = 0.0, si = 0.0;
-  for (int c = 0; c < BEOR_TB; ++c) {
-    double2 m = Mt[c * BEOR_TB + tid], q = xj[c];
-    if (I == J && c > tid) {   // upper part of a diagonal tile: use the Hermitian mirror
-      double2 mm = Mt[tid * BEOR_TB + c];
-      m = make_double2(mm.x, -mm.y);
-    }
-    sr = fma(m.x, q.x, fma(-m.y, q.y, sr));
-    si = fma(m.x, q.y, fma(m.y, q.x, si));
+}
+
+// hi + sm += (ah + al + at)(bh + bl + bt): the leading product split exactly
+// (p + e, FMA), the terms down to 2^-48 of it added to e, p added to hi by an
+// error-free two-sum whose error goes to sm (Ogita, Rump and Oishi, "Accurate
+// sum and dot product", SIAM J. Sci. Comput. 26 (2005), Dot2).
+__device__ __forceinline__ void dot2_mac(float& hi, float& sm, float ah, float al, float at, float bh, float bl,
+                                         float bt) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  e = fmaf(ah, bt, e);
+  e = fmaf(al, bl, e);
+  e = fmaf(at, bh, e);
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  sm += err + e;
+}
+
+// r_I -= sum_J M_IJ x_J for the problems of one work item, with float64-like
+// accuracy on the float32 pipe: M and x as exact float triples, Dot2 products
+// and sums within a 128-column tile, float64 totals across tiles and, across
+// work items, float64 atomics.  Thread (row r, half h) serves 8 problems.
+constexpr int RG = 16;   // problems per work item
+__global__ void __launch_bounds__(256, 2) resid_df_kernel(BatchView v) {
+  extern __shared__ float xs[];          // [RG][128][6]
+  __shared__ int64_t roff[RG];
+  const RWork w = v.rwork[blockIdx.x];
+  const SetDesc sd = v.sets[w.set];
+  const int r = threadIdx.x & (BEOR_TB - 1), half = threadIdx.x >> 7;
+  if (threadIdx.x < RG) {
+    const int q = threadIdx.x;
+    roff[q] = q < w.nb && v.status[w.p0 + q] <= 0 ? v.prob[w.p0 + q].row_off : (int64_t)-1;
   }
-  atomicAdd(&r[I * BEOR_TB + tid].x, -sr);
-  atomicAdd(&r[I * BEOR_TB + tid].y, -si);
-  if (I != J) {
-    // rows of block J: (M_IJ^H x_I)[c] = sum_r conj(M[r][c]) x_I[r]; one warp per column
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int c = warp; c < BEOR_TB; c += 4) {
-      double ar = 0.0, ai = 0.0;
-      for (int rr = lane; rr < BEOR_TB; rr += 32) {
-        double2 m = Mt[c * BEOR_TB + rr], q = xi[rr];
-        ar = fma(m.x, q.x, fma(m.y, q.y, ar));
-        ai = fma(m.x, q.y, fma(-m.y, q.x, ai));
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        ar += __shfl_xor_sync(0xffffffffu, ar, o);
-        ai += __shfl_xor_sync(0xffffffffu, ai, o);
-      }
-      if (lane == 0) {
-        atomicAdd(&r[J * BEOR_TB + c].x, -ar);
-        atomicAdd(&r[J * BEOR_TB + c].y, -ai);
+  double tre[8], tim[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) tre[q] = tim[q] = 0.0;
+  for (int J = w.j0; J < w.j1; ++J) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < RG * BEOR_TB * 6; e += blockDim.x) {
+      const int q = e / (BEOR_TB * 6), rem = e - q * (BEOR_TB * 6);
+      xs[e] = roff[q] >= 0 ? v.xtr[(roff[q] + (int64_t)J * BEOR_TB) * 6 + rem] : 0.0f;
+    }
+    __syncthreads();
+    const int64_t t0 = ((int64_t)w.I * sd.nt + J) * BEOR_TILE_ELEMS + r;
+    const float4* __restrict__ T4 = sd.Mf + t0;
+    const float2* __restrict__ T2 = sd.Mft + t0;
+    float hr[8], sr[8], hi[8], si[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) hr[q] = sr[q] = hi[q] = si[q] = 0.0f;
+#pragma unroll 2
+    for (int c = 0; c < BEOR_TB; ++c) {
+      const float4 m4 = __ldg(T4 + c * BEOR_TB);
+      const float2 m2 = __ldg(T2 + c * BEOR_TB);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float* x = xs + ((half * 8 + q) * BEOR_TB + c) * 6;
+        const float xrh = x[0], xrl = x[1], xrt = x[2], xih = x[3], xil = x[4], xit = x[5];
+        // re += mr xr - mi xi, im += mr xi + mi xr
+        dot2_mac(hr[q], sr[q], m4.x, m4.y, m2.x, xrh, xrl, xrt);
+        dot2_mac(hr[q], sr[q], -m4.z, -m4.w, -m2.y, xih, xil, xit);
+        dot2_mac(hi[q], si[q], m4.x, m4.y, m2.x, xih, xil, xit);
+        dot2_mac(hi[q], si[q], m4.z, m4.w, m2.y, xrh, xrl, xrt);
       }
     }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      tre[q] += (double)hr[q] + (double)sr[q];
+      tim[q] += (double)hi[q] + (double)si[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t ro = roff[half * 8 + q];
+    if (ro < 0) continue;
+    double2* dst = v.vec_r + ro + (int64_t)w.I * BEOR_TB + r;
+    atomicAdd(&dst->x, -tre[q]);
+    atomicAdd(&dst->y, -tim[q]);
   }
 }
 
@@ -859,9 +902,15 @@ __global__ void resid_norm_kernel(BatchView v) {
 }
 
 cudaError_t launch_residual(const BatchView& v, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(resid_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(float) * RG * BEOR_TB * 6));
+    attr = true;
+  }
   resid_init_kernel<<<dim3(8, v.P), 256, 0, s>>>(v);
-  int64_t tiles = tri_count(v.max_nt);
-  resid_tile_kernel<<<dim3(v.P, (unsigned)tiles), 128, 0, s>>>(v);
+  xsplit_kernel<<<dim3(8, v.P), 256, 0, s>>>(v);
+  resid_df_kernel<<<v.n_rwork, 256, sizeof(float) * RG * BEOR_TB * 6, s>>>(v);
   resid_norm_kernel<<<v.P, 256, 0, s>>>(v);
   return cudaGetLastError();
 }

@@ -194,6 +194,40 @@ __global__ void split_df_kernel(const double2* __restrict__ M, int64_t n, float4
 
 // ---------------------------------------------------------------------------
 // host launchers
+// Tile (I, J) of the full square, element (r, c) column-major: M_IJ for
+// I > J, conj(M_JI)^T for I < J, the Hermitian mirror of the stored lower
+// part inside diagonal tiles; entries beyond n are zero.  Each component
+// is split m = hi + lo + t exactly (hi = fl(m), lo = fl(m - hi), and the
+// remainder has at most 53 - 48 bits).
+__global__ void split_full_kernel(const double2* __restrict__ M, int n, int nt, float4* __restrict__ hl,
+                                  float2* __restrict__ tt) {
+  const int I = blockIdx.x / nt, J = blockIdx.x % nt;
+  const int64_t out0 = (int64_t)blockIdx.x * BEOR_TILE_ELEMS;
+  for (int e = threadIdx.x; e < BEOR_TILE_ELEMS; e += blockDim.x) {
+    const int c = e / BEOR_TB, r = e % BEOR_TB;
+    const int gr = I * BEOR_TB + r, gc = J * BEOR_TB + c;
+    double2 m = make_double2(0.0, 0.0);
+    if (gr < n && gc < n) {
+      if (gr >= gc) {
+        m = M[tri_index(I, J) * BEOR_TILE_ELEMS + (int64_t)c * BEOR_TB + r];
+      } else {
+        const double2 u = M[tri_index(J, I) * BEOR_TILE_ELEMS + (int64_t)r * BEOR_TB + c];
+        m = make_double2(u.x, -u.y);
+      }
+    }
+    const float rh = (float)m.x, ih = (float)m.y;
+    const double rd = m.x - (double)rh, id = m.y - (double)ih;
+    const float rl = (float)rd, il = (float)id;
+    hl[out0 + e] = make_float4(rh, rl, ih, il);
+    tt[out0 + e] = make_float2((float)(rd - (double)rl), (float)(id - (double)il));
+  }
+}
+
+cudaError_t split_full_triple(const double2* M, int n, int nt, float4* hl, float2* t, cudaStream_t s) {
+  split_full_kernel<<<nt * nt, 256, 0, s>>>(M, n, nt, hl, t);
+  return cudaGetLastError();
+}
+
 cudaError_t split_double_float(const double2* M, int64_t n, float4* out, cudaStream_t s) {
   split_df_kernel<<<1024, 256, 0, s>>>(M, n, out);
   return cudaGetLastError();
