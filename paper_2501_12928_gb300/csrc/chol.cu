@@ -470,7 +470,7 @@ cudaError_t launch_trail_f64(const BatchView& v, int k, cudaStream_t s) {
 // --------------------------------------------------------------------------
 struct CAcc {          // complex accumulator
   double2 d;           // float64 path
-  dfl re, im;          // double-float path
+  dfl re, im;          // double-float path: hi = error-free running sum, lo = its accumulated errors
 };
 
 __device__ __forceinline__ void cacc_zero(CAcc& a) {
@@ -485,32 +485,40 @@ __device__ __forceinline__ void cacc_mac(CAcc& a, const double2* L, double2 y, d
   a.d.x = fma(l.x, y.x, fma(-li, y.y, a.d.x));
   a.d.y = fma(l.x, y.y, fma(li, y.x, a.d.y));
 }
+// acc += (ah + al)(bh + bl) to about 2^-48 of the product: the leading
+// product split exactly by FMA, first-order terms added to its error, the
+// product summed by an error-free two-sum whose error goes to acc.lo (Dot2 of
+// Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)).
+__device__ __forceinline__ void dot2_acc(dfl& acc, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float s = acc.hi + p;
+  const float bb = s - acc.hi;
+  acc.lo += ((acc.hi - (s - bb)) + (p - bb)) + e;
+  acc.hi = s;
+}
 __device__ __forceinline__ void cacc_mac(CAcc& a, const float4* L, double2, dfl yr, dfl yi, bool conj_l) {
   const float4 l = *L;
-  const dfl lr{l.x, l.y};
-  const dfl li = conj_l ? dfl{-l.z, -l.w} : dfl{l.z, l.w};
-  a.re = df_add(a.re, df_add(df_mul(lr, yr), df_neg(df_mul(li, yi))));
-  a.im = df_add(a.im, df_add(df_mul(lr, yi), df_mul(li, yr)));
+  const float lih = conj_l ? -l.z : l.z, lil = conj_l ? -l.w : l.w;
+  // re += lr yr - li yi, im += lr yi + li yr
+  dot2_acc(a.re, l.x, l.y, yr.hi, yr.lo);
+  dot2_acc(a.re, -lih, -lil, yi.hi, yi.lo);
+  dot2_acc(a.im, l.x, l.y, yi.hi, yi.lo);
+  dot2_acc(a.im, lih, lil, yr.hi, yr.lo);
 }
 __device__ __forceinline__ double2 cacc_get(const CAcc& a, const double2*) { return a.d; }
 __device__ __forceinline__ double2 cacc_get(const CAcc& a, const float4*) {
-  return make_double2(df_to_double(a.re), df_to_double(a.im));
+  return make_double2((double)a.re.hi + (double)a.re.lo, (double)a.im.hi + (double)a.im.lo);
 }
 __device__ __forceinline__ void cacc_add(CAcc& a, const CAcc& b) {
   a.d.x += b.d.x;
   a.d.y += b.d.y;
-  a.re = df_add(a.re, b.re);
-  a.im = df_add(a.im, b.im);
-}
-__device__ __forceinline__ CAcc cacc_shfl_xor(const CAcc& a, int o) {
-  CAcc b;
-  b.d.x = __shfl_xor_sync(0xffffffffu, a.d.x, o);
-  b.d.y = __shfl_xor_sync(0xffffffffu, a.d.y, o);
-  b.re.hi = __shfl_xor_sync(0xffffffffu, a.re.hi, o);
-  b.re.lo = __shfl_xor_sync(0xffffffffu, a.re.lo, o);
-  b.im.hi = __shfl_xor_sync(0xffffffffu, a.im.hi, o);
-  b.im.lo = __shfl_xor_sync(0xffffffffu, a.im.lo, o);
-  return b;
+  dfl s = df_two_sum(a.re.hi, b.re.hi);
+  a.re = dfl{s.hi, s.lo + (a.re.lo + b.re.lo)};
+  s = df_two_sum(a.im.hi, b.im.hi);
+  a.im = dfl{s.hi, s.lo + (a.im.lo + b.im.lo)};
 }
 
 // y_blk = Linv (or Linv^H when herm) * r_blk, float64; 128 threads of the CTA
