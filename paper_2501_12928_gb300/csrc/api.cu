@@ -126,13 +126,15 @@ struct Plan {
   int prio_hi = 0;                  // greatest stream priority of the device
   std::vector<cudaEvent_t> pev;     // boundary events (profiling)
   std::vector<int> pcls;            // class of the launch after each boundary event
-  cudaStream_t side = nullptr;      // second stream of the look-ahead schedule
-  cudaEvent_t ev_col = nullptr, ev_rest = nullptr;
+  cudaStream_t side = nullptr;      // second stream of the look-ahead schedule (rest of the trailing update)
+  cudaStream_t side2 = nullptr;     // third stream: forward substitution of dbar, step by step
+  cudaEvent_t ev_col = nullptr, ev_rest = nullptr, ev_diag = nullptr, ev_fwd = nullptr;
   ~Plan() {
     for (cudaEvent_t e : pev) cudaEventDestroy(e);
-    if (ev_col) cudaEventDestroy(ev_col);
-    if (ev_rest) cudaEventDestroy(ev_rest);
+    for (cudaEvent_t e : {ev_col, ev_rest, ev_diag, ev_fwd})
+      if (e) cudaEventDestroy(e);
     if (side) cudaStreamDestroy(side);
+    if (side2) cudaStreamDestroy(side2);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (maps) mixed_maps_destroy(maps);
@@ -197,17 +199,28 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
   L += 2;
   RUN(KC_INIT, launch_copy_dbar(v, s));
   L += 1;
-  if (pl.mixed && pl.lookahead) {
-    // Look-ahead schedule of the mixed factorisation (two streams):
-    //   main: col(k) -> diag(k+1) -> slice(k+1) -> panel(k+1) -> slice(k+1) -> [rest(k)] col(k+1) ...
-    //   side: [col(k)] rest(k)
+  const bool la = pl.mixed && pl.lookahead;
+  if (la) {
+    // Look-ahead schedule of the mixed factorisation (three streams):
+    //   main:  col(k) -> diag(k+1) -> slice(k+1) -> panel(k+1) -> slice(k+1) -> [rest(k)] col(k+1) ...
+    //   side:  [col(k)] rest(k)
+    //   side2: [diag(k+1)] forward substitution step k of y = L^-1 dbar
     // col(k) updates block column k+1 only, rest(k) the columns j >= k+2, so
     // the float64 diagonal factorisation and the panel of step k+1 run at high
     // priority on the SMs that rest(k) leaves free; rest(k) takes its tiles
     // from a counter, so its CTAs that start late (after the high-priority
-    // kernels) just take fewer.
+    // kernels) just take fewer.  Forward step k needs only block column k
+    // (final after panel(k)) and the inverse diagonal block k+1.
     const int hi = pl.prio_hi;
+    auto fwd_after_diag = [&]() -> cudaError_t {
+      cudaError_t x = cudaEventRecord(pl.ev_diag, s);
+      if (x == cudaSuccess) x = cudaStreamWaitEvent(pl.side2, pl.ev_diag, 0);
+      return x;
+    };
     RUN(KC_DIAG, launch_diag(v, 0, true, s, hi));
+    L += 1;
+    if ((e = fwd_after_diag()) != cudaSuccess) return e;
+    RUN_ON(KC_SOLVE, pl.side2, launch_fwd_step(v, true, v.vec_b, -1, pl.side2));
     L += 1;
     if (pl.max_nt > 1) {
       RUN(KC_SLICE, launch_slice_panel(v, 0, s, hi));
@@ -222,6 +235,9 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
       if ((e = cudaStreamWaitEvent(pl.side, pl.ev_col, 0)) != cudaSuccess) return e;
       RUN(KC_DIAG, launch_diag(v, k + 1, true, s, hi));
       L += 1;
+      if ((e = fwd_after_diag()) != cudaSuccess) return e;
+      RUN_ON(KC_SOLVE, pl.side2, launch_fwd_step(v, true, v.vec_b, k, pl.side2));
+      L += 1;
       if (mixed_tiles(pl.maps, 1, k) > 0) {
         RUN_ON(KC_TRAIL, pl.side, launch_trail_mixed(v, pl.maps, k, TRAIL_REST, pl.side));
         L += 1;
@@ -235,6 +251,8 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
       }
       if ((e = cudaStreamWaitEvent(s, pl.ev_rest, 0)) != cudaSuccess) return e;
     }
+    if ((e = cudaEventRecord(pl.ev_fwd, pl.side2)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, pl.ev_fwd, 0)) != cudaSuccess) return e;
   } else {
     for (int k = 0; k < pl.max_nt; ++k) {
       RUN(KC_DIAG, launch_diag(v, k, pl.mixed, s));
@@ -254,8 +272,13 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
       }
     }
   }
-  RUN(KC_SOLVE, launch_solve(v, pl.mixed, v.vec_b, v.vec_x, s));
-  L += solve_launch_count(pl.max_nt);
+  if (la) {
+    RUN(KC_SOLVE, launch_bwd(v, true, v.vec_x, s));   // the forward half ran during the factorisation
+    L += pl.max_nt;
+  } else {
+    RUN(KC_SOLVE, launch_solve(v, pl.mixed, v.vec_b, v.vec_x, s));
+    L += solve_launch_count(pl.max_nt);
+  }
   const bool corr = pl.mixed && !pl.refine_x;
   if (pl.mixed && pl.refine_x) {
     // the solution itself is wanted (posterior mean): float64 iterative refinement
@@ -403,8 +426,9 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, Pla
     chk(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     pl->prio_hi = hi;
     chk(cudaStreamCreateWithPriority(&pl->side, cudaStreamNonBlocking, lo));
-    chk(cudaEventCreateWithFlags(&pl->ev_col, cudaEventDisableTiming));
-    chk(cudaEventCreateWithFlags(&pl->ev_rest, cudaEventDisableTiming));
+    chk(cudaStreamCreateWithPriority(&pl->side2, cudaStreamNonBlocking, lo));
+    for (cudaEvent_t* ev : {&pl->ev_col, &pl->ev_rest, &pl->ev_diag, &pl->ev_fwd})
+      chk(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
   }
   chk(cudaEventCreate(&pl->ev0));
   chk(cudaEventCreate(&pl->ev1));

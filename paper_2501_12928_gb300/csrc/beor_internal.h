@@ -82,6 +82,10 @@ cudaError_t launch_diag(const BatchView& v, int k, bool mixed, cudaStream_t s, i
 cudaError_t launch_panel_f64(const BatchView& v, int k, cudaStream_t s);
 cudaError_t launch_trail_f64(const BatchView& v, int k, cudaStream_t s);
 cudaError_t launch_solve(const BatchView& v, bool mixed, const double2* rhs, double2* out, cudaStream_t s);
+// The solve's two halves: forward step k (k = -1: start) of vec_y = L^-1 rhs,
+// and the whole backward pass out = L^-H vec_y.
+cudaError_t launch_fwd_step(const BatchView& v, bool mixed, const double2* rhs, int k, cudaStream_t s, int prio = 0);
+cudaError_t launch_bwd(const BatchView& v, bool mixed, double2* out, cudaStream_t s);
 int solve_launch_count(int max_nt);
 cudaError_t launch_lnl(const BatchView& v, cudaStream_t s, int corr);   // corr: residual-corrected q
 cudaError_t launch_solve_fwd(const BatchView& v, bool mixed, const double2* rhs, cudaStream_t s);   // vec_y = L^-1 rhs

@@ -521,6 +521,27 @@ __device__ __forceinline__ void cacc_add(CAcc& a, const CAcc& b) {
   a.im = dfl{s.hi, s.lo + (a.im.lo + b.im.lo)};
 }
 
+// sum over the 8 lanes of an aligned lane octet (xor 1, 2, 4)
+__device__ __forceinline__ void cacc_reduce8(CAcc& a, const double2*) {
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    a.d.x += __shfl_xor_sync(0xffffffffu, a.d.x, o);
+    a.d.y += __shfl_xor_sync(0xffffffffu, a.d.y, o);
+  }
+}
+__device__ __forceinline__ void cacc_reduce8(CAcc& a, const float4*) {
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    CAcc b;
+    b.d = make_double2(0.0, 0.0);
+    b.re.hi = __shfl_xor_sync(0xffffffffu, a.re.hi, o);
+    b.re.lo = __shfl_xor_sync(0xffffffffu, a.re.lo, o);
+    b.im.hi = __shfl_xor_sync(0xffffffffu, a.im.hi, o);
+    b.im.lo = __shfl_xor_sync(0xffffffffu, a.im.lo, o);
+    cacc_add(a, b);
+  }
+}
+
 // y_blk = Linv (or Linv^H when herm) * r_blk, float64; 128 threads of the CTA
 __device__ __forceinline__ void diag_apply(const double2* __restrict__ li, const double2* rk, double2* out,
                                            bool herm) {
@@ -641,37 +662,31 @@ __global__ void __launch_bounds__(256) bwd_step_kernel(BatchView v, int k, doubl
     xki[tid] = df_from_double(q.y);
   }
   __syncthreads();
-  // r_i[c] -= sum_m conj(L_ki[m][c]) x_k[m]: tile (k, i) column-major, so each
-  // column is contiguous.  Two passes of 64 columns through shared memory
-  // (row stride 129 elements: conflict-free column reads); thread (c, part)
-  // sums a quarter of m, four partial sums per column.
-  extern __shared__ __align__(16) unsigned char bsm_raw[];
-  WS* sm = reinterpret_cast<WS*>(bsm_raw);
-  CAcc* part_acc = reinterpret_cast<CAcc*>(bsm_raw + sizeof(WS) * 64 * 129);
+  // r_i[c] -= sum_m conj(L_ki[m][c]) x_k[m]: tile (k, i) is column-major, so
+  // column c is 128 contiguous elements.  A warp takes 4 columns at a time,
+  // 8 lanes per column on interleaved m (each load instruction reads four
+  // 128-byte segments), and sums the 8 partials by shuffles.
   const WS* t = reinterpret_cast<const WS*>(v.ws) + pr.ws_off + tri_index(k, i) * BEOR_TILE_ELEMS;
-  const int cc = tid & 63, part = tid >> 6;
-  for (int h = 0; h < 2; ++h) {
-    const WS* src = t + (int64_t)(64 * h) * BEOR_TB;
-    for (int e = tid; e < 64 * BEOR_TB; e += 256) sm[(e >> 7) * 129 + (e & 127)] = src[e];
-    __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, cl = lane >> 3, mo = lane & 7;
+#pragma unroll 1
+  for (int it = 0; it < 4; ++it) {
+    const int c = warp * 16 + it * 4 + cl;
     CAcc a;
     cacc_zero(a);
 #pragma unroll 4
-    for (int m = part * 32; m < part * 32 + 32; ++m) cacc_mac(a, sm + cc * 129 + m, xk[m], xkr[m], xki[m], true);
-    part_acc[tid] = a;
-    __syncthreads();
-    if (part == 0) {
-#pragma unroll
-      for (int q = 1; q < 4; ++q) cacc_add(a, part_acc[cc + 64 * q]);
+    for (int u = 0; u < 16; ++u) {
+      const int m = mo + 8 * u;
+      cacc_mac(a, t + c * BEOR_TB + m, xk[m], xkr[m], xki[m], true);
+    }
+    cacc_reduce8(a, t);
+    if (mo == 0) {
       const double2 sv = cacc_get(a, t);
-      const int c = 64 * h + cc;
       double2 cur = r[i * BEOR_TB + c];
       cur.x -= sv.x;
       cur.y -= sv.y;
       r[i * BEOR_TB + c] = cur;
       rk[c] = cur;
     }
-    __syncthreads();
   }
   if (i != k - 1) return;
   __syncthreads();
@@ -680,33 +695,40 @@ __global__ void __launch_bounds__(256) bwd_step_kernel(BatchView v, int k, doubl
   if (tid < BEOR_TB) x[i * BEOR_TB + tid] = xk[tid];
 }
 
-constexpr size_t kBwdSmem = 16 * 64 * 129 + sizeof(CAcc) * 256;
 
+// Forward step k of y = L^-1 rhs (k = -1: r = rhs and y_0), every problem.
+cudaError_t launch_fwd_step(const BatchView& v, bool mixed, const double2* rhs, int k, cudaStream_t s, int prio) {
+  const int nb = k < 0 ? v.max_nt : v.max_nt - k - 1;
+  if (nb <= 0) return cudaSuccess;
+  if (mixed) return launch_prio(fwd_step_kernel<float4>, dim3(nb, v.P), dim3(256), 0, s, prio, v, k, rhs);
+  return launch_prio(fwd_step_kernel<double2>, dim3(nb, v.P), dim3(256), 0, s, prio, v, k, rhs);
+}
+
+// out = L^-H y (y in vec_y), every problem.
 template <typename WS>
-static cudaError_t solve_impl(const BatchView& v, const double2* rhs, double2* out, bool back, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(bwd_step_kernel<WS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
-    attr = true;
-  }
+static cudaError_t bwd_impl(const BatchView& v, double2* out, cudaStream_t s) {
   const int nt = v.max_nt;
-  fwd_step_kernel<WS><<<dim3(nt, v.P), 256, 0, s>>>(v, -1, rhs);
-  for (int k = 0; k + 1 < nt; ++k) fwd_step_kernel<WS><<<dim3(nt - k - 1, v.P), 256, 0, s>>>(v, k, rhs);
-  if (!back) return cudaGetLastError();
-  bwd_step_kernel<WS><<<dim3(nt, v.P), 256, kBwdSmem, s>>>(v, nt, out);
+  bwd_step_kernel<WS><<<dim3(nt, v.P), 256, 0, s>>>(v, nt, out);
   for (int k = nt - 1; k >= 1; --k) {
     // problems whose last block is k-1 (nt_p == k) start here
-    bwd_step_kernel<WS><<<dim3(k, v.P), 256, kBwdSmem, s>>>(v, k, out);
+    bwd_step_kernel<WS><<<dim3(k, v.P), 256, 0, s>>>(v, k, out);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve(const BatchView& v, bool mixed, const double2* rhs, double2* out, cudaStream_t s) {
-  return mixed ? solve_impl<float4>(v, rhs, out, true, s) : solve_impl<double2>(v, rhs, out, true, s);
+cudaError_t launch_bwd(const BatchView& v, bool mixed, double2* out, cudaStream_t s) {
+  return mixed ? bwd_impl<float4>(v, out, s) : bwd_impl<double2>(v, out, s);
 }
 
 cudaError_t launch_solve_fwd(const BatchView& v, bool mixed, const double2* rhs, cudaStream_t s) {
-  return mixed ? solve_impl<float4>(v, rhs, nullptr, false, s) : solve_impl<double2>(v, rhs, nullptr, false, s);
+  cudaError_t e = cudaSuccess;
+  for (int k = -1; k + 1 < v.max_nt && e == cudaSuccess; ++k) e = launch_fwd_step(v, mixed, rhs, k, s, 0);
+  return e;
+}
+
+cudaError_t launch_solve(const BatchView& v, bool mixed, const double2* rhs, double2* out, cudaStream_t s) {
+  cudaError_t e = launch_solve_fwd(v, mixed, rhs, s);
+  return e == cudaSuccess ? launch_bwd(v, mixed, out, s) : e;
 }
 
 int solve_launch_count(int max_nt) { return 2 * max_nt; }
