@@ -102,4 +102,47 @@ __device__ __forceinline__ dfl df_from_double(double x) {
 }
 __device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
 
+// acc += (ah + al)(bh + bl) to about 2^-48 of the product: the leading
+// product split exactly by FMA, first-order terms added to its error, the
+// product summed by an error-free two-sum whose error goes to acc.lo (Dot2 of
+// Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)).
+__device__ __forceinline__ void dot2_acc(dfl& acc, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float s = acc.hi + p;
+  const float bb = s - acc.hi;
+  acc.lo += ((acc.hi - (s - bb)) + (p - bb)) + e;
+  acc.hi = s;
+}
+
+// acc += (ah + al + at)(bh + bl): as dot2_acc, with the second-order terms
+// al bl and at bh also added to the leading product's error.
+__device__ __forceinline__ void dot2_acc3(dfl& acc, float ah, float al, float at, float bh, float bl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  e = fmaf(al, bl, e);
+  e = fmaf(at, bh, e);
+  const float s = acc.hi + p;
+  const float bb = s - acc.hi;
+  acc.lo += ((acc.hi - (s - bb)) + (p - bb)) + e;
+  acc.hi = s;
+}
+
+// round(a + b) to the nearest integer for a double-float a + b (|b| at most
+// half an ulp of a, |a + b| < 2^62): each part is rounded, and the sum of
+// the two residuals (each exact in fp32, within [-1/2, 1/2]) decides a
+// final step of one.  fp32 and integer operations only.
+__device__ __forceinline__ long long round_df(float a, float b) {
+  const float ra = rintf(a), rb = rintf(b);
+  long long x = (long long)ra + (long long)rb;
+  const float d = (a - ra) + (b - rb);
+  if (d > 0.5f) ++x;
+  else if (d < -0.5f) --x;
+  return x;
+}
+
 }  // namespace beor

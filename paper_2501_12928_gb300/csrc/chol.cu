@@ -151,32 +151,10 @@ cudaError_t launch_prior_init(const BatchView& v, bool mixed, cudaStream_t s) {
 }
 
 // --------------------------------------------------------------------------
-// bf16 slicing of one row of 128 complex values (mixed path operands).
-// value = 2^(e-7) * sum_s slice_s, slice_s = sigma_s * 2^(-8 s), sigma_s an
-// integer with |sigma_s| <= 128; exact in float64 arithmetic.
-// --------------------------------------------------------------------------
-__device__ __forceinline__ int row_exponent(double mx) {
-  if (!(mx > 0.0)) return -1000;
-  return ilogb(mx) + 1;
-}
-// Balanced base-256 digits of the 64-bit fixed-point number round(x * 2^(39 - e)):
-// one float64 scaling and conversion, then integer arithmetic.
-__device__ __forceinline__ void slice_value(double x, int e, __nv_bfloat16* out, int64_t plane_stride) {
-  long long X = e <= -1000 ? 0 : llrint(ldexp(x, 39 - e));
-  int dg[BEOR_NSLICE];
-#pragma unroll
-  for (int s = BEOR_NSLICE - 1; s >= 1; --s) {
-    const long long m = ((X + 128) & 255) - 128;
-    dg[s] = (int)m;
-    X = (X - m) >> 8;
-  }
-  dg[0] = (int)X;
-#pragma unroll
-  for (int s = 0; s < BEOR_NSLICE; ++s) out[s * plane_stride] = __float2bfloat16_rn(ldexpf((float)dg[s], -8 * s));
-}
-
-// --------------------------------------------------------------------------
-// diagonal block: float64 Cholesky + inverse, log-det, status
+// diagonal block: float64 Cholesky, log-det, status, and the inverse of the
+// block (float64; on the mixed path formed on the fp32 pipe) with, on the
+// mixed path, the bf16 slices of its rows: value = 2^(e-7) sum_s sigma_s
+// 2^(-8 s), sigma_s integers with |sigma_s| <= 128.
 // --------------------------------------------------------------------------
 #define DG_PACK (BEOR_TB * (BEOR_TB + 1) / 2)
 __device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
@@ -257,58 +235,137 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
     ws_store(ws + e, r >= c ? A[pk(r, c)] : make_double2(0.0, 0.0));
   }
   __syncthreads();
-  // in-place inverse, row by row: Linv[i][j] = -(sum_{m=j}^{i-1} L[i][m] Linv[m][j]) / L[i][i];
-  // four threads share each dot product (thread = 4 j + part)
-  const int jj = tid >> 2, part = tid & 3;
-  for (int i = 0; i < BEOR_TB; ++i) {
-    const double lii = A[pk(i, i)].x;
-    double sr = 0.0, si = 0.0;
-    if (jj < i) {
-      for (int m = jj + part; m < i; m += 4) {
-        const double2 a = A[pk(i, m)], b = A[pk(m, jj)];
-        sr = fma(a.x, b.x, fma(-a.y, b.y, sr));
-        si = fma(a.x, b.y, fma(a.y, b.x, si));
+  if (!mixed) {
+    // in-place inverse, row by row: Linv[i][j] = -(sum_{m=j}^{i-1} L[i][m] Linv[m][j]) / L[i][i];
+    // four threads share each dot product (thread = 4 j + part)
+    const int jj = tid >> 2, part = tid & 3;
+    for (int i = 0; i < BEOR_TB; ++i) {
+      const double lii = A[pk(i, i)].x;
+      double sr = 0.0, si = 0.0;
+      if (jj < i) {
+        for (int m = jj + part; m < i; m += 4) {
+          const double2 a = A[pk(i, m)], b = A[pk(m, jj)];
+          sr = fma(a.x, b.x, fma(-a.y, b.y, sr));
+          si = fma(a.x, b.y, fma(a.y, b.x, si));
+        }
       }
+      sr += __shfl_xor_sync(0xffffffffu, sr, 1);
+      si += __shfl_xor_sync(0xffffffffu, si, 1);
+      sr += __shfl_xor_sync(0xffffffffu, sr, 2);
+      si += __shfl_xor_sync(0xffffffffu, si, 2);
+      __syncthreads();
+      if (jj < i && part == 0) {
+        const double inv = 1.0 / lii;
+        A[pk(i, jj)] = make_double2(-sr * inv, -si * inv);
+      }
+      if (tid == 0) A[pk(i, i)] = make_double2(1.0 / lii, 0.0);
+      __syncthreads();
     }
-    sr += __shfl_xor_sync(0xffffffffu, sr, 1);
-    si += __shfl_xor_sync(0xffffffffu, si, 1);
-    sr += __shfl_xor_sync(0xffffffffu, sr, 2);
-    si += __shfl_xor_sync(0xffffffffu, si, 2);
-    __syncthreads();
-    if (jj < i && part == 0) {
-      const double inv = 1.0 / lii;
-      A[pk(i, jj)] = make_double2(-sr * inv, -si * inv);
+    double2* dinv = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
+    for (int e = tid; e < DG_PACK; e += nthr) dinv[e] = A[e];
+    return;
+  }
+  // Mixed path: the inverse feeds the 40-bit panel slices and the
+  // double-float solves only, so it is formed on the fp32 pipe instead of in
+  // float64, whose rate on this GPU is 1/64 of fp32.  L is split exactly into
+  // three floats per component: {re hi, re lo, im hi, im lo} in place (16
+  // bytes per element either way) and the third terms in Lt.  Each product
+  // L[i][m] Linv[m][j] keeps the terms down to 2^-48 of its leading part
+  // (Dot2 accumulation); Linv itself is held as double-float.
+  float4* Af = reinterpret_cast<float4*>(A);
+  float2* Lt = reinterpret_cast<float2*>(col + BEOR_TB);
+  for (int e = tid; e < DG_PACK; e += nthr) {
+    const double2 a = A[e];
+    const float rh = (float)a.x, ih = (float)a.y;
+    const double rd = a.x - (double)rh, id = a.y - (double)ih;
+    const float rl = (float)rd, il = (float)id;
+    Af[e] = make_float4(rh, rl, ih, il);
+    Lt[e] = make_float2((float)(rd - (double)rl), (float)(id - (double)il));
+  }
+  __shared__ dfl s_inv;
+  __syncthreads();
+  {
+    const int jj = tid >> 2, part = tid & 3;
+    for (int i = 0; i < BEOR_TB; ++i) {
+      if (tid == 0) {
+        const float4 d = Af[pk(i, i)];
+        s_inv = df_from_double(1.0 / ((double)d.x + (double)d.y + (double)Lt[pk(i, i)].x));
+      }
+      dfl sr{0.0f, 0.0f}, si{0.0f, 0.0f};
+      if (jj < i) {
+        for (int m = jj + part; m < i; m += 4) {
+          const float4 a = Af[pk(i, m)], b = Af[pk(m, jj)];
+          const float2 at = Lt[pk(i, m)];
+          dot2_acc3(sr, a.x, a.y, at.x, b.x, b.y);
+          dot2_acc3(sr, -a.z, -a.w, -at.y, b.z, b.w);
+          dot2_acc3(si, a.x, a.y, at.x, b.z, b.w);
+          dot2_acc3(si, a.z, a.w, at.y, b.x, b.y);
+        }
+      }
+#pragma unroll
+      for (int o = 1; o <= 2; o <<= 1) {
+        dfl t = df_two_sum(sr.hi, __shfl_xor_sync(0xffffffffu, sr.hi, o));
+        sr = dfl{t.hi, t.lo + (sr.lo + __shfl_xor_sync(0xffffffffu, sr.lo, o))};
+        t = df_two_sum(si.hi, __shfl_xor_sync(0xffffffffu, si.hi, o));
+        si = dfl{t.hi, t.lo + (si.lo + __shfl_xor_sync(0xffffffffu, si.lo, o))};
+      }
+      __syncthreads();
+      if (jj < i && part == 0) {
+        const dfl inv = s_inv;
+        const dfl qr = df_mul(df_fast_two_sum(sr.hi, sr.lo), inv);
+        const dfl qi = df_mul(df_fast_two_sum(si.hi, si.lo), inv);
+        Af[pk(i, jj)] = make_float4(-qr.hi, -qr.lo, -qi.hi, -qi.lo);
+      }
+      if (tid == 0) Af[pk(i, i)] = make_float4(s_inv.hi, s_inv.lo, 0.0f, 0.0f);
+      __syncthreads();
     }
-    if (tid == 0) A[pk(i, i)] = make_double2(1.0 / lii, 0.0);
-    __syncthreads();
   }
   double2* dinv = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
-  for (int e = tid; e < DG_PACK; e += nthr) dinv[e] = A[e];
-  if (mixed) {
-    // slices of Linv rows (B operand of the panel product L_ik = A_ik Linv^H)
-    if (tid < BEOR_TB) {
-      const int c = tid;
-      double mx = 0.0;
-      for (int m = 0; m <= c; ++m) {
-        double2 a = A[pk(c, m)];
-        mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
-      }
-      int e = row_exponent(mx);
-      const int64_t row = (int64_t)p * BEOR_TB + c;
-      const int64_t lrows = (int64_t)v.P * BEOR_TB;
-      v.linv_exp[row] = e;
-      const int64_t ps = lrows * BEOR_TB;   // planes [part][slice]: slice stride is one plane
-      for (int m = 0; m < BEOR_TB; ++m) {
-        double2 a = m <= c ? A[pk(c, m)] : make_double2(0.0, 0.0);
-        slice_value(a.x, e, v.linv_sl + (0 * BEOR_NSLICE * lrows + row) * BEOR_TB + m, ps);
-        slice_value(a.y, e, v.linv_sl + (1 * BEOR_NSLICE * lrows + row) * BEOR_TB + m, ps);
+  for (int e = tid; e < DG_PACK; e += nthr) {
+    const float4 f = Af[e];
+    dinv[e] = make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
+  }
+  // slices of Linv rows (B operand of the panel product L_ik = A_ik Linv^H):
+  // balanced base-256 digits of round(x * 2^(39 - e)), x = hi + lo (scaled
+  // exactly by a power of two, rounded once)
+  const int64_t lrows = (int64_t)v.P * BEOR_TB;
+  const int64_t ps = lrows * BEOR_TB;   // planes [part][slice]: slice stride is one plane
+  for (int c = warp; c < BEOR_TB; c += nwarp) {
+    float mx = 0.0f;
+    for (int m = lane; m <= c; m += 32) {
+      const float4 a = Af[pk(c, m)];
+      mx = fmaxf(mx, fmaxf(fabsf(a.x), fabsf(a.z)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = mx > 0.0f ? ilogbf(mx) + 1 : -1000;
+    const int64_t row = (int64_t)p * BEOR_TB + c;
+    if (lane == 0) v.linv_exp[row] = e;
+    for (int m = lane; m < BEOR_TB; m += 32) {
+      const float4 a = m <= c ? Af[pk(c, m)] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        const float hi = part ? a.z : a.x, lo = part ? a.w : a.y;
+        long long X = 0;
+        if (e > -1000) X = round_df(ldexpf(hi, 39 - e), ldexpf(lo, 39 - e));
+        int dg[BEOR_NSLICE];
+#pragma unroll
+        for (int sl = BEOR_NSLICE - 1; sl >= 1; --sl) {
+          const long long mm = ((X + 128) & 255) - 128;
+          dg[sl] = (int)mm;
+          X = (X - mm) >> 8;
+        }
+        dg[0] = (int)X;
+        __nv_bfloat16* dst = v.linv_sl + (part * BEOR_NSLICE * lrows + row) * BEOR_TB + m;
+#pragma unroll
+        for (int sl = 0; sl < BEOR_NSLICE; ++sl) dst[sl * ps] = __float2bfloat16_rn(ldexpf((float)dg[sl], -8 * sl));
       }
     }
   }
 }
 
 cudaError_t launch_diag(const BatchView& v, int k, bool mixed, cudaStream_t s, int prio) {
-  const size_t smem = sizeof(double2) * (DG_PACK + BEOR_TB);
+  // packed block, one column, and (mixed) the third float terms of L
+  const size_t smem = sizeof(double2) * (DG_PACK + BEOR_TB) + sizeof(float2) * DG_PACK;
   static bool init = false;
   if (!init) {
     cudaFuncSetAttribute(diag_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -484,20 +541,6 @@ __device__ __forceinline__ void cacc_mac(CAcc& a, const double2* L, double2 y, d
   const double li = conj_l ? -l.y : l.y;
   a.d.x = fma(l.x, y.x, fma(-li, y.y, a.d.x));
   a.d.y = fma(l.x, y.y, fma(li, y.x, a.d.y));
-}
-// acc += (ah + al)(bh + bl) to about 2^-48 of the product: the leading
-// product split exactly by FMA, first-order terms added to its error, the
-// product summed by an error-free two-sum whose error goes to acc.lo (Dot2 of
-// Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)).
-__device__ __forceinline__ void dot2_acc(dfl& acc, float ah, float al, float bh, float bl) {
-  const float p = ah * bh;
-  float e = fmaf(ah, bh, -p);
-  e = fmaf(ah, bl, e);
-  e = fmaf(al, bh, e);
-  const float s = acc.hi + p;
-  const float bb = s - acc.hi;
-  acc.lo += ((acc.hi - (s - bb)) + (p - bb)) + e;
-  acc.hi = s;
 }
 __device__ __forceinline__ void cacc_mac(CAcc& a, const float4* L, double2, dfl yr, dfl yi, bool conj_l) {
   const float4 l = *L;

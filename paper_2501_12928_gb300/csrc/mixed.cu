@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(256)
         const float hi = part ? a.z : a.x, lo = part ? a.w : a.y;
         // balanced base-256 digits of the fixed-point number round(x * 2^(39 - e))
         long long X = 0;
-        if (e > -1000) X = llrintf(ldexpf(hi, 39 - e)) + llrintf(ldexpf(lo, 39 - e));
+        if (e > -1000) X = round_df(ldexpf(hi, 39 - e), ldexpf(lo, 39 - e));
         int dg[BEOR_NSLICE];
 #pragma unroll
         for (int sl = BEOR_NSLICE - 1; sl >= 1; --sl) {
