@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
   double2* A = dsm;                    // packed lower 128x128
   double2* col = dsm + DG_PACK;        // 128
   __shared__ int s_fail;
+  __shared__ double s_rinv;            // 1 / L_jj of the current column
   const int p = blockIdx.x;
   const Prob pr = v.prob[p];
   if (k >= pr.nt) return;
@@ -184,12 +185,14 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
       if (!(d > 0.0) || !isfinite(d)) {
         s_fail = k * BEOR_TB + j + 1;
       } else {
-        A[pk(j, j)] = make_double2(sqrt(d), 0.0);
+        const double l = sqrt(d);
+        A[pk(j, j)] = make_double2(l, 0.0);
+        s_rinv = 1.0 / l;   // one float64 division per column, not one per thread
       }
     }
     __syncthreads();
     if (s_fail) break;
-    const double inv = 1.0 / A[pk(j, j)].x;
+    const double inv = s_rinv;
     for (int i = j + 1 + tid; i < BEOR_TB; i += nthr) {
       double2 a = A[pk(i, j)];
       a.x *= inv;
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
     // four threads share each dot product (thread = 4 j + part)
     const int jj = tid >> 2, part = tid & 3;
     for (int i = 0; i < BEOR_TB; ++i) {
-      const double lii = A[pk(i, i)].x;
+      if (tid == 0) s_rinv = 1.0 / A[pk(i, i)].x;
       double sr = 0.0, si = 0.0;
       if (jj < i) {
         for (int m = jj + part; m < i; m += 4) {
@@ -255,10 +258,10 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
       si += __shfl_xor_sync(0xffffffffu, si, 2);
       __syncthreads();
       if (jj < i && part == 0) {
-        const double inv = 1.0 / lii;
+        const double inv = s_rinv;
         A[pk(i, jj)] = make_double2(-sr * inv, -si * inv);
       }
-      if (tid == 0) A[pk(i, i)] = make_double2(1.0 / lii, 0.0);
+      if (tid == 0) A[pk(i, i)] = make_double2(s_rinv, 0.0);
       __syncthreads();
     }
     double2* dinv = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
