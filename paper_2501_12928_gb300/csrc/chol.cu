@@ -201,11 +201,17 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
       col[i] = a;
     }
     __syncthreads();
-    // rank-1 update of the trailing lower triangle: A_il -= L_ij conj(L_lj), 4 FMAs each
-    for (int i = j + 1 + warp; i < BEOR_TB; i += nwarp) {
-      const double2 ai = col[i];
-      for (int l = j + 1 + lane; l <= i; l += 32) {
-        const double2 al = col[l];
+    // rank-1 update of the trailing lower triangle: A_il -= L_ij conj(L_lj), 4 FMAs each;
+    // the triangle's elements are dealt out in order, so every lane has work
+    {
+      const int nt1 = BEOR_TB - 1 - j;
+      const int total = nt1 * (nt1 + 1) / 2;
+      for (int e = tid; e < total; e += nthr) {
+        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (a * (a + 1) / 2 > e) --a;
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        const int i = j + 1 + a, l = j + 1 + (e - a * (a + 1) / 2);
+        const double2 ai = col[i], al = col[l];
         double2 x = A[pk(i, l)];
         x.x = fma(-ai.x, al.x, fma(-ai.y, al.y, x.x));
         x.y = fma(-ai.y, al.x, fma(ai.x, al.y, x.y));
@@ -288,29 +294,51 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
   __shared__ dfl s_inv;
   __syncthreads();
   {
+    // four threads share each dot product (thread = 4 jj + part); each keeps
+    // eight independent Dot2 chains (re/im x product x m parity), combined
+    // by exact two-sums, to shorten the dependent-add latency
     const int jj = tid >> 2, part = tid & 3;
     for (int i = 0; i < BEOR_TB; ++i) {
       if (tid == 0) {
         const float4 d = Af[pk(i, i)];
         s_inv = df_from_double(1.0 / ((double)d.x + (double)d.y + (double)Lt[pk(i, i)].x));
       }
-      dfl sr{0.0f, 0.0f}, si{0.0f, 0.0f};
+      dfl c[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) c[q] = dfl{0.0f, 0.0f};
       if (jj < i) {
-        for (int m = jj + part; m < i; m += 4) {
+        int m = jj + part;
+        for (; m + 4 < i; m += 8) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int mm = m + 4 * h;
+            const float4 a = Af[pk(i, mm)], b = Af[pk(mm, jj)];
+            const float2 at = Lt[pk(i, mm)];
+            dot2_acc3(c[4 * h + 0], a.x, a.y, at.x, b.x, b.y);
+            dot2_acc3(c[4 * h + 1], -a.z, -a.w, -at.y, b.z, b.w);
+            dot2_acc3(c[4 * h + 2], a.x, a.y, at.x, b.z, b.w);
+            dot2_acc3(c[4 * h + 3], a.z, a.w, at.y, b.x, b.y);
+          }
+        }
+        if (m < i) {
           const float4 a = Af[pk(i, m)], b = Af[pk(m, jj)];
           const float2 at = Lt[pk(i, m)];
-          dot2_acc3(sr, a.x, a.y, at.x, b.x, b.y);
-          dot2_acc3(sr, -a.z, -a.w, -at.y, b.z, b.w);
-          dot2_acc3(si, a.x, a.y, at.x, b.z, b.w);
-          dot2_acc3(si, a.z, a.w, at.y, b.x, b.y);
+          dot2_acc3(c[0], a.x, a.y, at.x, b.x, b.y);
+          dot2_acc3(c[1], -a.z, -a.w, -at.y, b.z, b.w);
+          dot2_acc3(c[2], a.x, a.y, at.x, b.z, b.w);
+          dot2_acc3(c[3], a.z, a.w, at.y, b.x, b.y);
         }
       }
+      auto add = [](dfl x, dfl y) {
+        const dfl t = df_two_sum(x.hi, y.hi);
+        return dfl{t.hi, t.lo + (x.lo + y.lo)};
+      };
+      dfl sr = add(add(c[0], c[1]), add(c[4], c[5]));
+      dfl si = add(add(c[2], c[3]), add(c[6], c[7]));
 #pragma unroll
       for (int o = 1; o <= 2; o <<= 1) {
-        dfl t = df_two_sum(sr.hi, __shfl_xor_sync(0xffffffffu, sr.hi, o));
-        sr = dfl{t.hi, t.lo + (sr.lo + __shfl_xor_sync(0xffffffffu, sr.lo, o))};
-        t = df_two_sum(si.hi, __shfl_xor_sync(0xffffffffu, si.hi, o));
-        si = dfl{t.hi, t.lo + (si.lo + __shfl_xor_sync(0xffffffffu, si.lo, o))};
+        sr = add(sr, dfl{__shfl_xor_sync(0xffffffffu, sr.hi, o), __shfl_xor_sync(0xffffffffu, sr.lo, o)});
+        si = add(si, dfl{__shfl_xor_sync(0xffffffffu, si.hi, o), __shfl_xor_sync(0xffffffffu, si.lo, o)});
       }
       __syncthreads();
       if (jj < i && part == 0) {
