@@ -179,18 +179,23 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
   if (tid == 0) s_fail = 0;
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
-  for (int j = 0; j < BEOR_TB; ++j) {
-    if (tid == 0) {
-      const double d = A[pk(j, j)].x;
-      if (!(d > 0.0) || !isfinite(d)) {
-        s_fail = k * BEOR_TB + j + 1;
-      } else {
-        const double l = sqrt(d);
-        A[pk(j, j)] = make_double2(l, 0.0);
-        s_rinv = 1.0 / l;   // one float64 division per column, not one per thread
-      }
+  // Pivot of column j (thread 0): L_jj = sqrt(a_jj) and 1 / L_jj, or failure.
+  // Column j+1's pivot is taken right after its diagonal element's last
+  // update (element 0 of step j's update, also thread 0), so the square root
+  // and division overlap the other threads' updates instead of running alone.
+  auto pivot = [&](int j) {
+    const double d = A[pk(j, j)].x;
+    if (!(d > 0.0) || !isfinite(d)) {
+      s_fail = k * BEOR_TB + j + 1;
+    } else {
+      const double l = sqrt(d);
+      A[pk(j, j)] = make_double2(l, 0.0);
+      s_rinv = 1.0 / l;   // one float64 division per column, not one per thread
     }
-    __syncthreads();
+  };
+  if (tid == 0) pivot(0);
+  __syncthreads();
+  for (int j = 0; j < BEOR_TB; ++j) {
     if (s_fail) break;
     const double inv = s_rinv;
     for (int i = j + 1 + tid; i < BEOR_TB; i += nthr) {
@@ -216,6 +221,7 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
         x.x = fma(-ai.x, al.x, fma(-ai.y, al.y, x.x));
         x.y = fma(-ai.y, al.x, fma(ai.x, al.y, x.y));
         A[pk(i, l)] = x;
+        if (e == 0) pivot(j + 1);   // element 0 is (j+1, j+1), now final
       }
     }
     __syncthreads();
@@ -291,7 +297,12 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
     Af[e] = make_float4(rh, rl, ih, il);
     Lt[e] = make_float2((float)(rd - (double)rl), (float)(id - (double)il));
   }
-  __shared__ dfl s_inv;
+  __shared__ dfl s_invs[BEOR_TB];      // 1 / L_ii for every row, formed in parallel
+  __syncthreads();                     // the split of L is complete
+  if (tid < BEOR_TB) {
+    const float4 d = Af[pk(tid, tid)];
+    s_invs[tid] = df_from_double(1.0 / ((double)d.x + (double)d.y + (double)Lt[pk(tid, tid)].x));
+  }
   __syncthreads();
   {
     // four threads share each dot product (thread = 4 jj + part); each keeps
@@ -299,10 +310,6 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
     // by exact two-sums, to shorten the dependent-add latency
     const int jj = tid >> 2, part = tid & 3;
     for (int i = 0; i < BEOR_TB; ++i) {
-      if (tid == 0) {
-        const float4 d = Af[pk(i, i)];
-        s_inv = df_from_double(1.0 / ((double)d.x + (double)d.y + (double)Lt[pk(i, i)].x));
-      }
       dfl c[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) c[q] = dfl{0.0f, 0.0f};
@@ -342,12 +349,12 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
       }
       __syncthreads();
       if (jj < i && part == 0) {
-        const dfl inv = s_inv;
+        const dfl inv = s_invs[i];
         const dfl qr = df_mul(df_fast_two_sum(sr.hi, sr.lo), inv);
         const dfl qi = df_mul(df_fast_two_sum(si.hi, si.lo), inv);
         Af[pk(i, jj)] = make_float4(-qr.hi, -qr.lo, -qi.hi, -qi.lo);
       }
-      if (tid == 0) Af[pk(i, i)] = make_float4(s_inv.hi, s_inv.lo, 0.0f, 0.0f);
+      if (tid == 0) Af[pk(i, i)] = make_float4(s_invs[i].hi, s_invs[i].lo, 0.0f, 0.0f);
       __syncthreads();
     }
   }
