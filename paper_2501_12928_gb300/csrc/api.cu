@@ -347,6 +347,10 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, Pla
   }
   pl->P = (int)pl->h_prob.size();
   pl->rows = rows;
+  // mixed batches of uneven sizes: each problem starts max_nt - nt block steps
+  // late, so that all end on the last step and the light late steps of the
+  // largest problems overlap the heavy early steps of the smaller ones
+  for (Prob& pr : pl->h_prob) pr.k_off = pl->mixed ? pl->max_nt - pr.nt : 0;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) {
     if (x != cudaSuccess && e == cudaSuccess) e = x;

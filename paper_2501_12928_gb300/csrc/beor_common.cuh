@@ -33,6 +33,9 @@ struct Prob {
   int64_t ws_off;     // element offset of tile (0,0) in the workspace
   int64_t dinv_off;   // element offset (double2) of this problem's inverse diagonal blocks
   int64_t row_off;    // row offset of this problem in the panel-slice and vector buffers
+  int k_off;          // block step of the batch at which this problem's step 0 runs (mixed:
+                      // max nt - nt, so that all problems end together); kernels given the
+                      // batch's step kg work on the problem's step kg - k_off
 };
 
 // One instrument (shared by all prior points of the set).

@@ -160,7 +160,7 @@ cudaError_t launch_prior_init(const BatchView& v, bool mixed, cudaStream_t s) {
 __device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
 
 template <typename WS>
-__global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed) {
+__global__ void __launch_bounds__(512) diag_kernel(BatchView v, int kg, int mixed) {
   extern __shared__ double2 dsm[];
   double2* A = dsm;                    // packed lower 128x128
   double2* col = dsm + DG_PACK;        // 128
@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int k, int mixed
   __shared__ double s_rinv;            // 1 / L_jj of the current column
   const int p = blockIdx.x;
   const Prob pr = v.prob[p];
-  if (k >= pr.nt) return;
+  const int k = kg - pr.k_off;   // this problem's block step
+  if (k < 0 || k >= pr.nt) return;
   if (v.status[p] != 0) return;
   WS* ws = reinterpret_cast<WS*>(v.ws) + pr.ws_off + tri_index(k, k) * BEOR_TILE_ELEMS;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -417,14 +418,15 @@ cudaError_t launch_diag(const BatchView& v, int k, bool mixed, cudaStream_t s, i
 // --------------------------------------------------------------------------
 // float64 panel: L_ik = A_ik Linv_kk^H for i > k (rows split in two halves)
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) panel_f64_kernel(BatchView v, int k) {
+__global__ void __launch_bounds__(256) panel_f64_kernel(BatchView v, int kg) {
   extern __shared__ double2 psm[];
   double2* xs = psm;                  // [128 m][64 r]
   double2* ys = psm + 128 * 64;       // [16 m][128 c]
   const int p = blockIdx.y;
   const Prob pr = v.prob[p];
+  const int k = kg - pr.k_off;
   const int i = k + 1 + (blockIdx.x >> 1);
-  if (i >= pr.nt || v.status[p] != 0) return;
+  if (k < 0 || i >= pr.nt || v.status[p] != 0) return;
   const int r0 = (blockIdx.x & 1) * 64;
   double2* tile = reinterpret_cast<double2*>(v.ws) + pr.ws_off + tri_index(i, k) * BEOR_TILE_ELEMS;
   const double2* linv = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
@@ -486,12 +488,13 @@ cudaError_t launch_panel_f64(const BatchView& v, int k, cudaStream_t s) {
 // --------------------------------------------------------------------------
 // float64 trailing update: A_ij -= L_ik L_jk^H, k < j <= i, 64 x 64 sub-tiles
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) trail_f64_kernel(BatchView v, int k) {
+__global__ void __launch_bounds__(256) trail_f64_kernel(BatchView v, int kg) {
   __shared__ double2 xs[16][64];
   __shared__ double2 ys[16][64];
   const int p = blockIdx.y;
   const Prob pr = v.prob[p];
-  const int T = pr.nt - k - 1;
+  const int k = kg - pr.k_off;
+  const int T = k < 0 ? 0 : pr.nt - k - 1;
   const int64_t t = blockIdx.x >> 2;
   if (T <= 0 || t >= tri_count(T) || v.status[p] != 0) return;
   const int si = (blockIdx.x >> 1) & 1, sj = blockIdx.x & 1;
@@ -648,13 +651,15 @@ __device__ __forceinline__ void diag_apply(const double2* __restrict__ li, const
 // Forward step k (k = -1: only y_0).  CTA (i, p), i = k+1 .. nt-1:
 // r_i -= L_ik y_k; the CTA with i == k+1 then sets y_{k+1} = Linv r_{k+1}.
 template <typename WS>
-__global__ void __launch_bounds__(256) fwd_step_kernel(BatchView v, int k, const double2* __restrict__ rhs) {
+__global__ void __launch_bounds__(256) fwd_step_kernel(BatchView v, int kg, const double2* __restrict__ rhs) {
   __shared__ double2 yk[BEOR_TB];
   __shared__ dfl ykr[BEOR_TB], yki[BEOR_TB];
   __shared__ CAcc part[BEOR_TB];
   __shared__ double2 rk[BEOR_TB];
   const int p = blockIdx.y;
   const Prob pr = v.prob[p];
+  const int k = kg - pr.k_off;   // this problem's step (-1: start)
+  if (k < -1) return;
   const int i = k + 1 + blockIdx.x;
   if (i >= pr.nt || v.status[p] > 0) return;
   const int tid = threadIdx.x;

@@ -242,6 +242,7 @@ __device__ __forceinline__ bool decode_tile(const BatchView& v, const int64_t* p
   const int p = lo;
   int64_t u = t - prefix[p];
   if (v.status[p] > 0) return false;
+  k -= v.prob[p].k_off;   // this problem's block step
   jb.p = p;
   jb.h = (int)(u % (BEOR_TB / MX_N));
   u /= (BEOR_TB / MX_N);
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       const int e_r = pexp[pr.row_off + (int64_t)jb.i * BEOR_TB + r];
       const int32_t* ecol = MODE == MODE_TRAIL ? pexp + pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N
                                                : v.linv_exp + (int64_t)jb.p * BEOR_TB + jb.h * MX_N;
-      const int out_j = MODE == MODE_TRAIL ? jb.j : k;
+      const int out_j = jb.j;   // trail: block column j; panel: the panel column
       float4* __restrict__ C = reinterpret_cast<float4*>(v.ws) + pr.ws_off + tri_index(jb.i, out_j) * BEOR_TILE_ELEMS +
                   (int64_t)(jb.h * MX_N) * BEOR_TB + r;
       const uint32_t trow = tmem + ((uint32_t)lane_base << 16);
@@ -555,13 +556,14 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 // slicing of the panel rows: rows of tiles (i, k), i > k, of every problem
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-    slice_panel_kernel(BatchView v, int k, __nv_bfloat16* __restrict__ panel_sl, int32_t* __restrict__ panel_exp) {
+    slice_panel_kernel(BatchView v, int kg, __nv_bfloat16* __restrict__ panel_sl, int32_t* __restrict__ panel_exp) {
   constexpr int R = 16;                     // rows per block
   __shared__ float4 s[BEOR_TB][R + 1];      // [column][row], padded
   const int p = blockIdx.y;
   const Prob pr = v.prob[p];
+  const int k = kg - pr.k_off;   // this problem's block step
   const int i = k + 1 + blockIdx.x / (BEOR_TB / R);
-  if (i >= pr.nt || v.status[p] > 0) return;
+  if (k < 0 || i >= pr.nt || v.status[p] > 0) return;
   const int r0 = (blockIdx.x % (BEOR_TB / R)) * R;
   const float4* tile = reinterpret_cast<const float4*>(v.ws) + pr.ws_off + tri_index(i, k) * BEOR_TILE_ELEMS;
   for (int e = threadIdx.x; e < BEOR_TB * R; e += 256) {
@@ -679,7 +681,8 @@ cudaError_t mixed_maps_create(const BatchView& v, MixedMaps** out) {
     for (int k = 0; k < v.max_nt; ++k) {
       int64_t* pk = pre.data() + ((size_t)kind * v.max_nt + k) * (v.P + 1);
       for (int p = 0; p < v.P; ++p) {
-        const int64_t T = std::max(0, hp[p].nt - k - 1);   // block rows below the diagonal
+        const int kp = k - hp[p].k_off;                      // the problem's own block step
+        const int64_t T = kp < 0 ? 0 : std::max(0, hp[p].nt - kp - 1);   // block rows below the diagonal
         int64_t n = 0;
         if (kind == KIND_COL || kind == KIND_PANEL) n = T;
         else if (kind == KIND_REST) n = tri_count((int)std::max<int64_t>(0, T - 1));
