@@ -138,7 +138,7 @@ int beor_get_dbar(beor_ctx *ctx, beor_c128 *dbar_out);
 /* Diagnostics of the last lnL / posterior-mean call on this context.
  * ms_class / n_class: device time and launch count per kernel class
  * (0 prior+init, 1 diagonal block, 2 slicing, 3 panel, 4 trailing update,
- * 5 triangular solves, 6 refinement residual/update, 7 lnL), filled only
+ * 5 triangular solves, 6 float64-accurate residual (and refinement update), 7 lnL), filled only
  * when profiling is on (beor_set_profiling); ms_last is -1 on the call that
  * captures a batch's graph. */
 typedef struct {

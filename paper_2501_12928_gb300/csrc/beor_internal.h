@@ -37,14 +37,14 @@ struct BatchView {
   double2* vec_y;            // [rows] forward-solve result
   double2* vec_x;            // [rows] solution
   double2* vec_t;            // [rows] solve scratch
-  double2* vec_r;            // [rows] refinement residual
+  double2* vec_r;            // [rows] residual dbar - Sigma x (lnL correction or refinement)
   double2* vec_d;            // [rows] refinement correction
   double* logdet_phi;        // [P]
   double* logdet_sigma;      // [P]
   double* q;                 // [P]
   double* lnl;               // [P]
   int32_t* status;           // [P]
-  double* resid;             // [P] refinement residual norm ratio
+  double* resid;             // [P] accuracy indicator (see beor_stats.resid_rel_max)
   Flags* flags;
   // mixed path slice buffers
   __nv_bfloat16* panel_sl;   // 2 buffers (block step parity) of [NPLANE][rows][128], plane = part * NSLICE + slice

@@ -5,11 +5,12 @@
 // Kernels here serve both precisions:
 //  * prior / init:  Phi^-1 from phi (one amplitude per k bin, Eq. for P(k_i)),
 //                   log|Phi|, and the working matrix W = M + diag(Phi^-1);
-//  * diag:          float64 factorisation and inversion of the 128 x 128
-//                   diagonal block, log|Sigma| accumulation, status;
+//  * diag:          float64 factorisation of the 128 x 128 diagonal block,
+//                   log|Sigma| accumulation, status, and its inverse (float64;
+//                   on the fp32 pipe, with bf16 slices, on the mixed path);
 //  * panel/trail:   float64 tile GEMMs (the float64 comparator path);
 //  * solve:         blocked forward / backward substitution;
-//  * lnl:           q = Re(dbar^H abar) and lnL.
+//  * lnl:           q = Re(dbar^H abar), or its residual-corrected form, and lnL.
 #include <algorithm>
 #include <cmath>
 
