@@ -8,7 +8,10 @@ caption).  From the weighted posterior samples this module gives, per bin:
 * P(k_i) = 10^phi_i and the dimensionless power
   Delta^2(k_i) = k_i^3 P(k_i) / (2 pi^2) (Sec. "Statement of need", the
   equation after the spherical average P(k_i)), each with quantiles;
-* a check of an injected spectrum against those intervals.
+* a check of an injected spectrum against those intervals;
+* Bayes factors between models from their evidences (Sec. "Summary": the
+  evidence makes the package usable for model selection), including a
+  point-null model whose evidence is its likelihood at one parameter value.
 
 k is in whatever units the caller's bin centres use (the synthetic
 instruments use uv-eta grid units).  Host-side post-processing of sampler
@@ -95,3 +98,13 @@ def format_table(summary, qs=(0.16, 0.5, 0.84)):
                      + " ".join(f"{v:.4g}" for v in b.p_q) + "   "
                      + " ".join(f"{v:.4g}" for v in b.delta2_q))
     return "\n".join(lines)
+
+
+def log_bayes_factor(logz_a: float, logz_b: float) -> float:
+    """ln K = ln Z_a - ln Z_b: K > 1 favours model a."""
+    return float(logz_a) - float(logz_b)
+
+
+def point_null_logz(loglike, phi) -> float:
+    """Evidence of a model with no free parameters (phi fixed): Z = L(phi)."""
+    return float(np.asarray(loglike(np.atleast_2d(np.asarray(phi, float))), float)[0])

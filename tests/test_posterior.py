@@ -6,8 +6,8 @@ import math
 import numpy as np
 import pytest
 
-from paper_2501_12928_gb300.posterior import (delta_squared, injected_within, power_spectrum_posterior,
-                                              weighted_quantiles)
+from paper_2501_12928_gb300.posterior import (delta_squared, injected_within, log_bayes_factor,
+                                              point_null_logz, power_spectrum_posterior, weighted_quantiles)
 
 
 def test_equal_weights_are_hazen_quantiles():
@@ -62,3 +62,16 @@ def test_bad_inputs_raise():
         weighted_quantiles([1.0, 2.0], [1.0, -1.0], [0.5])
     with pytest.raises(ValueError):
         power_spectrum_posterior(np.zeros((4, 2)), np.ones(4), [1.0, 2.0, 3.0])
+
+
+def test_bayes_factor_and_point_null():
+    assert log_bayes_factor(10.0, 4.5) == 5.5
+    # a point-null model's evidence is its likelihood at the fixed parameters
+    calls = []
+
+    def loglike(x):
+        calls.append(x.copy())
+        return -0.5 * np.sum(x * x, axis=1)
+
+    assert point_null_logz(loglike, [1.0, 2.0]) == pytest.approx(-2.5)
+    assert calls[0].shape == (1, 2)
