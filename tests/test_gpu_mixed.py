@@ -141,3 +141,31 @@ def test_lookahead_schedule_is_bitwise_in_order(P):
     assert err.max() <= ATOL_LNL, err
     st = likes[0].stats()
     assert st["n_class"]["trail"] > 0 and st["ms_class"]["trail"] > 0
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_ragged_batches_across_sets(P, precision):
+    """Uneven sizes (1, 3 and 9 block steps) with ragged batch sizes per set
+    (1, 17 and 5 points: the 17 span two 16-point residual work groups),
+    every point against the oracle."""
+    specs = ((90, 70, 2, 1), (400, 383, 3, 17), (1300, 1100, 5, 5))
+    likes, phs, refs = [], [], []
+    for nvis, n, nk, B in specs:
+        p = random_problem(nvis, n, nk, seed=n + 11)
+        lk = P.Likelihood(precision)
+        lk.set_T(p["T"], p["kbin"], nk, 2.0)
+        lk.set_data(p["d"], p["noise_var"])
+        lk.precompute()
+        ph = np.random.default_rng(n + 5).uniform(-2, 2, (B, nk))
+        M = O.herm_dense(p["T"], p["noise_var"])
+        db = O.dbar_dense(p["T"], p["noise_var"], p["d"])
+        refs.append(np.array([O.evaluate(M, db, p["kbin"], q, 2.0)["lnl"] for q in ph]))
+        likes.append(lk)
+        phs.append(ph)
+    outs, sts = P.lnl_multi(likes, phs)
+    for o, st, r in zip(outs, sts, refs):
+        assert np.all(st == 0), st
+        if precision == "fp64":
+            assert np.all(np.abs(o - r) <= 1e-10 * np.abs(r)), np.abs(o - r) / np.abs(r)
+        else:
+            assert np.abs(o - r).max() <= ATOL_LNL, np.abs(o - r)
