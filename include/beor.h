@@ -123,6 +123,24 @@ int beor_lnl(beor_ctx *ctx, const double *phi, int B, double *lnl_out, int32_t *
 int beor_lnl_multi(beor_ctx *const *ctxs, int n_sets, const double *const *phi, const int *B,
                    double *const *lnl_out, int32_t *const *status_out, void *stream);
 
+/* Asynchronous form of beor_lnl_multi, for callers with several independent
+ * batches (e.g. a sampler's training set): `slot` (0..3) selects one of up
+ * to four independent copies of the batch's workspaces, so that batches
+ * enqueued on different streams with different slots run concurrently and
+ * the latency-bound last block steps of one overlap the heavy steps of the
+ * next.  phi, lnl_out and status_out must be device memory (BEOR_EINVAL
+ * otherwise).  The first call for a batch shape and slot runs synchronously
+ * (it captures the batch's graph); later calls return once the work is
+ * enqueued on `stream`, and the outputs are valid when the stream reaches
+ * that point.  Calls on one slot must be ordered (same stream, or ordered
+ * by the caller); calls on different slots share only read-only data.
+ * beor_lnl_multi_wait synchronises `stream` and reports a bounded
+ * device-side wait that gave up (BEOR_ETIMEOUT); beor_get_stats reflects
+ * synchronous calls only. */
+int beor_lnl_multi_async(beor_ctx *const *ctxs, int n_sets, const double *const *phi, const int *B,
+                         double *const *lnl_out, int32_t *const *status_out, int slot, void *stream);
+int beor_lnl_multi_wait(beor_ctx *const *ctxs, int n_sets, const int *B, int slot, void *stream);
+
 /* Posterior mean (maximum-a-posteriori amplitudes) abar = Sigma^-1 dbar for
  * one prior point phi (n_k).  abar_out: n_model complex (host or device). */
 int beor_posterior_mean(beor_ctx *ctx, const double *phi, beor_c128 *abar_out,

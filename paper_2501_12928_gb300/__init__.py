@@ -10,6 +10,8 @@ from .beor import (  # noqa: F401
     Emulator,
     lib,
     lnl_multi,
+    lnl_multi_async,
+    lnl_multi_wait,
     PREC_FP64,
     PREC_MIXED,
     KERNEL_CLASSES,

@@ -42,6 +42,8 @@ def _load():
         "beor_precompute": [_P, _P],
         "beor_lnl": [_P, _P, _c.c_int, _P, _P, _P],
         "beor_lnl_multi": [_P, _c.c_int, _P, _P, _P, _P, _P],
+        "beor_lnl_multi_async": [_P, _c.c_int, _P, _P, _P, _P, _c.c_int, _P],
+        "beor_lnl_multi_wait": [_P, _c.c_int, _P, _c.c_int, _P],
         "beor_posterior_mean": [_P, _P, _P, _P, _P],
         "beor_get_model_dims": [_P, _c.POINTER(_I64), _c.POINTER(_I64), _c.POINTER(_c.c_int)],
         "beor_get_M": [_P, _P],
@@ -105,6 +107,8 @@ def set_lookahead(on: bool):
 
 def _stream(stream):
     if stream is not None:
+        if hasattr(stream, "cuda_stream"):     # a torch.cuda.Stream
+            return ctypes.c_void_p(int(stream.cuda_stream))
         return ctypes.c_void_p(int(stream))
     try:
         import torch
@@ -257,6 +261,41 @@ def lnl_multi(likes: list, phis: list, stream=None):
                                  ctypes.cast(Bs, ctypes.c_void_p), ctypes.cast(op, ctypes.c_void_p),
                                  ctypes.cast(sp, ctypes.c_void_p), _stream(stream)), "beor_lnl_multi")
     return outs, sts
+
+
+def _dev_ptr(x):
+    """Address of a tensor-like object (data_ptr()), a numpy array, or an integer
+    (the library rejects host memory where it needs device memory)."""
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    return int(x)
+
+
+def lnl_multi_async(likes: list, phis: list, outs: list, sts: list, slot: int, stream):
+    """Enqueue one batched evaluation without waiting (device buffers only:
+    phis[s] (B_s, n_k) float64, outs[s] (B_s,) float64, sts[s] (B_s,) int32,
+    e.g. torch CUDA tensors).  See beor_lnl_multi_async in include/beor.h."""
+    n = len(likes)
+    ctxs = (ctypes.c_void_p * n)(*[lk._h.value for lk in likes])
+    Bs = (ctypes.c_int * n)(*[int(p.shape[0]) for p in phis])
+    pp = (ctypes.c_void_p * n)(*[_dev_ptr(p) for p in phis])
+    op = (ctypes.c_void_p * n)(*[_dev_ptr(o) for o in outs])
+    sp = (ctypes.c_void_p * n)(*[_dev_ptr(x) for x in sts])
+    _check(_lib().beor_lnl_multi_async(ctypes.cast(ctxs, ctypes.c_void_p), n, ctypes.cast(pp, ctypes.c_void_p),
+                                       ctypes.cast(Bs, ctypes.c_void_p), ctypes.cast(op, ctypes.c_void_p),
+                                       ctypes.cast(sp, ctypes.c_void_p), int(slot), _stream(stream)),
+           "beor_lnl_multi_async")
+
+
+def lnl_multi_wait(likes: list, Bs: list, slot: int, stream):
+    """Wait for the slot's enqueued work on `stream`; raises on a device timeout."""
+    n = len(likes)
+    ctxs = (ctypes.c_void_p * n)(*[lk._h.value for lk in likes])
+    bb = (ctypes.c_int * n)(*[int(b) for b in Bs])
+    _check(_lib().beor_lnl_multi_wait(ctypes.cast(ctxs, ctypes.c_void_p), n, ctypes.cast(bb, ctypes.c_void_p),
+                                      int(slot), _stream(stream)), "beor_lnl_multi_wait")
 
 
 class Emulator:

@@ -122,6 +122,7 @@ struct Plan {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool prof = false;
   bool refine_x = false;            // mixed: refine the solution (posterior mean) rather than correct q
+  int slot = 0;                     // independent copies of one batch shape (asynchronous calls)
   bool lookahead = true;            // schedule of the mixed factorisation captured in the graph
   int prio_hi = 0;                  // greatest stream priority of the device
   std::vector<cudaEvent_t> pev;     // boundary events (profiling)
@@ -303,9 +304,10 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
   return cudaSuccess;
 }
 
-int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, Plan** out) {
+int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, int slot, Plan** out) {
   Plan* pl = new Plan();
   pl->refine_x = need_x;
+  pl->slot = slot;
   pl->device = ctxs[0]->device;
   pl->mixed = ctxs[0]->precision == BEOR_PREC_MIXED;
   int64_t ws_elems = 0, dinv_elems = 0, rows = 0;
@@ -444,9 +446,9 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, Pla
   return BEOR_OK;
 }
 
-Plan* find_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x) {
+Plan* find_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, int slot) {
   for (Plan* p : g_plans) {
-    if ((int)p->ctxs.size() != nsets || p->refine_x != need_x) continue;
+    if ((int)p->ctxs.size() != nsets || p->refine_x != need_x || p->slot != slot) continue;
     bool same = true;
     for (int s = 0; s < nsets && same; ++s) same = p->ctxs[s] == ctxs[s] && p->Bs[s] == Bs[s];
     if (same) return p;
@@ -665,8 +667,16 @@ int beor_precompute(beor_ctx* c, void* stream) {
 }
 
 static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const* phi, const int* B,
-                          double* const* lnl_out, int32_t* const* status_out, void* stream, bool need_x) {
+                          double* const* lnl_out, int32_t* const* status_out, void* stream, bool need_x,
+                          int slot = 0, bool async = false) {
   if (!ctxs || nsets <= 0 || !phi || !B) return BEOR_EINVAL;
+  if (async) {
+    if (!lnl_out || !status_out) return BEOR_EINVAL;
+    for (int s = 0; s < nsets; ++s)
+      if (!phi[s] || !lnl_out[s] || !status_out[s] || !is_device_ptr(phi[s]) || !is_device_ptr(lnl_out[s]) ||
+          !is_device_ptr(status_out[s]))
+        return BEOR_EINVAL;
+  }
   for (int s = 0; s < nsets; ++s) {
     int r = check_ready(ctxs[s]);
     if (r) return r;
@@ -679,9 +689,9 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(g_mu);
   need_x = need_x && ctxs[0]->precision == BEOR_PREC_MIXED;
-  Plan* pl = find_plan(ctxs, nsets, B, need_x);
+  Plan* pl = find_plan(ctxs, nsets, B, need_x, slot);
   if (!pl) {
-    int r = build_plan(ctxs, nsets, B, need_x, &pl);
+    int r = build_plan(ctxs, nsets, B, need_x, slot, &pl);
     if (r) return r;
     g_plans.push_back(pl);
   }
@@ -694,6 +704,7 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
     }
     CKC(c0, to_device(pl->phis.as<double>() + pl->phi_off[s], phi[s], bytes, st));
   }
+  const bool first_use = !pl->exec;
   if (!pl->exec) {
     // first use: run once directly (sets kernel attributes), then capture
     int64_t nl = 0;
@@ -727,6 +738,9 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
     if (status_out && status_out[s])
       CKC(c0, from_device(status_out[s], pl->view.status + f, sizeof(int32_t) * B[s], st));
   }
+  // asynchronous call on a captured batch: done once the work is enqueued
+  // (errors of bounded device waits are reported by beor_lnl_multi_wait)
+  if (async && pl->launches > 0 && pl->exec && !first_use) return BEOR_OK;
   CKC(c0, cudaStreamSynchronize(st));
   CKC(c0, cudaGetLastError());
   {
@@ -780,6 +794,32 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
 int beor_lnl_multi(beor_ctx* const* ctxs, int nsets, const double* const* phi, const int* B,
                    double* const* lnl_out, int32_t* const* status_out, void* stream) {
   return lnl_multi_impl(ctxs, nsets, phi, B, lnl_out, status_out, stream, false);
+}
+
+int beor_lnl_multi_async(beor_ctx* const* ctxs, int nsets, const double* const* phi, const int* B,
+                         double* const* lnl_out, int32_t* const* status_out, int slot, void* stream) {
+  if (slot < 0 || slot >= 4) return BEOR_EINVAL;
+  return lnl_multi_impl(ctxs, nsets, phi, B, lnl_out, status_out, stream, false, slot, true);
+}
+
+int beor_lnl_multi_wait(beor_ctx* const* ctxs, int nsets, const int* B, int slot, void* stream) {
+  if (!ctxs || nsets <= 0 || !B || slot < 0 || slot >= 4) return BEOR_EINVAL;
+  Plan* pl = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    pl = find_plan(ctxs, nsets, B, false, slot);
+  }
+  if (!pl) return BEOR_ESTATE;
+  beor_ctx* c0 = ctxs[0];
+  cudaSetDevice(c0->device);
+  CKC(c0, cudaStreamSynchronize((cudaStream_t)stream));
+  int err = 0;
+  CKC(c0, cudaMemcpy(&err, &pl->view.flags->error, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    for (int s = 0; s < nsets; ++s) ctxs[s]->poisoned = true;
+    return BEOR_ETIMEOUT;
+  }
+  return BEOR_OK;
 }
 
 int beor_lnl(beor_ctx* c, const double* phi, int B, double* lnl_out, int32_t* status_out, void* stream) {

@@ -169,3 +169,27 @@ def test_ragged_batches_across_sets(P, precision):
             assert np.all(np.abs(o - r) <= 1e-10 * np.abs(r)), np.abs(o - r) / np.abs(r)
         else:
             assert np.abs(o - r).max() <= ATOL_LNL, np.abs(o - r)
+
+
+def test_async_slots_match_synchronous(P):
+    """Two batches in flight on two slots and two streams give the same lnL
+    as the synchronous call (the factorisation is deterministic; the float64
+    residual sums tiles in no fixed order), twice in a row."""
+    import torch
+    likes, phs, refs = _uneven_batch(P)
+    sync_out, _ = P.lnl_multi(likes, phs)
+    dev_phi = [torch.tensor(p, dtype=torch.float64, device="cuda") for p in phs]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [[torch.empty(len(p), dtype=torch.float64, device="cuda") for p in phs] for _ in range(2)]
+    sts = [[torch.empty(len(p), dtype=torch.int32, device="cuda") for p in phs] for _ in range(2)]
+    Bs = [len(p) for p in phs]
+    for _ in range(2):
+        for slot in (0, 1):
+            P.lnl_multi_async(likes, dev_phi, outs[slot], sts[slot], slot, streams[slot])
+        for slot in (0, 1):
+            P.lnl_multi_wait(likes, Bs, slot, streams[slot])
+            got = np.concatenate([o.cpu().numpy() for o in outs[slot]])
+            assert all(int((s != 0).sum()) == 0 for s in sts[slot])
+            assert np.allclose(got, np.concatenate(sync_out), rtol=1e-12, atol=0)
+    with pytest.raises(P.BeorError):      # host buffers are rejected
+        P.lnl_multi_async(likes, [np.ascontiguousarray(p) for p in phs], outs[0], sts[0], 0, streams[0])
