@@ -284,6 +284,16 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   auto job_full = [&](uint32_t q) { return bar0 + 8u * (9 + q); };
   auto job_empty = [&](uint32_t q) { return bar0 + 8u * (13 + q); };
 
+  // After a bounded wait gave up anywhere in this evaluation, the remaining
+  // launches return at once (read by one thread, so the whole CTA agrees)
+  // instead of each running into its own deadline.
+  {
+    __shared__ int s_err;
+    if (threadIdx.x == 0) s_err = *reinterpret_cast<volatile int*>(&v.flags->error);
+    __syncthreads();
+    if (s_err) return;
+  }
+
   if (threadIdx.x == 0) {
     for (int s = 0; s < MX_STAGES; ++s) {
       mbar_init(full_bar(s), 1);
