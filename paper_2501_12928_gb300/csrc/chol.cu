@@ -181,49 +181,80 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int kg, int mixe
   if (tid == 0) s_fail = 0;
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
-  // Pivot of column j (thread 0): L_jj = sqrt(a_jj) and 1 / L_jj, or failure.
-  // Column j+1's pivot is taken right after its diagonal element's last
-  // update (element 0 of step j's update, also thread 0), so the square root
-  // and division overlap the other threads' updates instead of running alone.
-  auto pivot = [&](int j) {
-    const double d = A[pk(j, j)].x;
-    if (!(d > 0.0) || !isfinite(d)) {
-      s_fail = k * BEOR_TB + j + 1;
-    } else {
-      const double l = sqrt(d);
-      A[pk(j, j)] = make_double2(l, 0.0);
-      s_rinv = 1.0 / l;   // one float64 division per column, not one per thread
+  // Right-looking Cholesky, two columns per pass (rank-2 updates): half the
+  // barriers and shared-memory round trips of one column per pass, with the
+  // same operations in the same order as the rank-1 sequence (identical
+  // results).  Thread 0 takes both pivots: L_jj, column j's element in row
+  // j+1 and its update of a_{j+1,j+1}, then L_{j+1,j+1}.
+  double2* col2 = col + BEOR_TB;   // column j+1 (this space later holds the mixed path's third terms of L)
+  __shared__ double s_rinv2;
+  for (int j = 0; j < BEOR_TB; j += 2) {
+    if (tid == 0) {
+      const double d = A[pk(j, j)].x;
+      if (!(d > 0.0) || !isfinite(d)) {
+        s_fail = k * BEOR_TB + j + 1;
+      } else {
+        const double l = sqrt(d);
+        A[pk(j, j)] = make_double2(l, 0.0);
+        const double rinv = 1.0 / l;
+        s_rinv = rinv;
+        double2 a = A[pk(j + 1, j)];
+        a.x *= rinv;
+        a.y *= rinv;
+        A[pk(j + 1, j)] = a;
+        col[j + 1] = a;
+        double2 x = A[pk(j + 1, j + 1)];
+        x.x = fma(-a.x, a.x, fma(-a.y, a.y, x.x));
+        x.y = fma(-a.y, a.x, fma(a.x, a.y, x.y));
+        const double d2 = x.x;
+        if (!(d2 > 0.0) || !isfinite(d2)) {
+          s_fail = k * BEOR_TB + j + 2;
+        } else {
+          const double l2 = sqrt(d2);
+          A[pk(j + 1, j + 1)] = make_double2(l2, 0.0);
+          s_rinv2 = 1.0 / l2;
+        }
+      }
     }
-  };
-  if (tid == 0) pivot(0);
-  __syncthreads();
-  for (int j = 0; j < BEOR_TB; ++j) {
+    __syncthreads();
     if (s_fail) break;
-    const double inv = s_rinv;
-    for (int i = j + 1 + tid; i < BEOR_TB; i += nthr) {
+    const double inv = s_rinv, inv2 = s_rinv2;
+    const double2 lj1 = col[j + 1];   // L_{j+1,j}
+    // columns j and j+1 below the pair: scale column j, apply it to column
+    // j+1 (the rank-1 step's update of those elements), scale column j+1
+    for (int i = j + 2 + tid; i < BEOR_TB; i += nthr) {
       double2 a = A[pk(i, j)];
       a.x *= inv;
       a.y *= inv;
       A[pk(i, j)] = a;
       col[i] = a;
+      double2 b = A[pk(i, j + 1)];
+      b.x = fma(-a.x, lj1.x, fma(-a.y, lj1.y, b.x));
+      b.y = fma(-a.y, lj1.x, fma(a.x, lj1.y, b.y));
+      b.x *= inv2;
+      b.y *= inv2;
+      A[pk(i, j + 1)] = b;
+      col2[i] = b;
     }
     __syncthreads();
-    // rank-1 update of the trailing lower triangle: A_il -= L_ij conj(L_lj), 4 FMAs each;
-    // the triangle's elements are dealt out in order, so every lane has work
+    // rank-2 update of the trailing lower triangle (rows and columns >= j+2):
+    // A_il -= L_ij conj(L_lj), then -= L_i,j+1 conj(L_l,j+1); the triangle's
+    // elements are dealt out in order, so every lane has work
     {
-      const int nt1 = BEOR_TB - 1 - j;
-      const int total = nt1 * (nt1 + 1) / 2;
+      const int nt2 = BEOR_TB - 2 - j;
+      const int total = nt2 * (nt2 + 1) / 2;
       for (int e = tid; e < total; e += nthr) {
         int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
         while (a * (a + 1) / 2 > e) --a;
         while ((a + 1) * (a + 2) / 2 <= e) ++a;
-        const int i = j + 1 + a, l = j + 1 + (e - a * (a + 1) / 2);
-        const double2 ai = col[i], al = col[l];
+        const int i = j + 2 + a, l = j + 2 + (e - a * (a + 1) / 2);
+        const double2 ai = col[i], al = col[l], bi = col2[i], bl = col2[l];
         double2 x = A[pk(i, l)];
         x.x = fma(-ai.x, al.x, fma(-ai.y, al.y, x.x));
         x.y = fma(-ai.y, al.x, fma(ai.x, al.y, x.y));
+        x.x = fma(-bi.x, bl.x, fma(-bi.y, bl.y, x.x));
+        x.y = fma(-bi.y, bl.x, fma(bi.x, bl.y, x.y));
         A[pk(i, l)] = x;
-        if (e == 0) pivot(j + 1);   // element 0 is (j+1, j+1), now final
       }
     }
     __syncthreads();
