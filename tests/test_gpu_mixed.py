@@ -193,3 +193,44 @@ def test_async_slots_match_synchronous(P):
             assert np.allclose(got, np.concatenate(sync_out), rtol=1e-12, atol=0)
     with pytest.raises(P.BeorError):      # host buffers are rejected
         P.lnl_multi_async(likes, [np.ascontiguousarray(p) for p in phs], outs[0], sts[0], 0, streams[0])
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_singular_point_is_isolated(P, precision):
+    """A point at which Sigma is singular gets status j > 0 and lnL = -inf,
+    and the other points of the batch are unaffected.  Columns 0 and 1 of T
+    are equal (2 at visibility 0, unit noise variance there), so
+    M_00 = M_01 = M_11 = 4 exactly; phi = 400 makes Phi^-1 of their k bin
+    underflow to 0, and the second pivot is 4 - 2 * 2 = 0 exactly in any
+    correctly rounded arithmetic: status 2, the oracle's too.  With 300
+    modes the failed point is carried through three block steps."""
+    p = random_problem(400, 300, 3, seed=5)
+    T, nv, kbin = p["T"].copy(), p["noise_var"].copy(), p["kbin"].copy()
+    T[:, 0] = 0.0
+    T[0, 0] = 2.0
+    T[:, 1] = T[:, 0]
+    nv[0] = 1.0
+    kbin[1] = 0
+    lk = P.Likelihood(precision)
+    lk.set_T(T, kbin, 3, 2.0)
+    lk.set_data(p["d"], nv)
+    lk.precompute()
+    ph = np.array([[0.3, -0.5, 1.0], [400.0, -0.5, 1.0], [-1.0, 0.7, 0.2]])
+    got, st = lk.lnl(ph)
+    M = O.herm_dense(T, nv)
+    db = O.dbar_dense(T, nv, p["d"])
+    ref = [O.evaluate(M, db, kbin, x, 2.0) for x in ph]
+    assert [r["status"] for r in ref] == [0, 2, 0]
+    assert list(st) == [0, 2, 0], st
+    assert got[1] == -np.inf
+    tol = ATOL_LNL if precision == "mixed" else 1e-10 * max(abs(ref[0]["lnl"]), abs(ref[2]["lnl"]))
+    for i in (0, 2):
+        assert abs(got[i] - ref[i]["lnl"]) <= tol, (i, got[i], ref[i]["lnl"])
+
+
+def test_empty_batch_is_rejected(P):
+    """B = 0 is an argument error (BEOR_EINVAL), not an empty launch."""
+    lk = make_like(P, "C0", precision="mixed")
+    with pytest.raises(P.BeorError, match=r"\(-1\)"):
+        lk.lnl(np.zeros((0, 4)))
+
