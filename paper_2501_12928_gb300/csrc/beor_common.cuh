@@ -19,6 +19,17 @@
 #define BEOR_NSLICE 5                     // bf16 slices per real value (mixed path)
 #define BEOR_NPLANE (2 * BEOR_NSLICE)     // (slice, re/im) planes
 
+// Element (row, col) of one bf16 slice plane of `rows` rows x 128 columns
+// (col = the GEMM's K index).  The plane is stored in the order in which the
+// tensor cores read it from shared memory, so that one K-chunk of 16 columns
+// for a block of rows is a contiguous range:
+//   [K-chunk col/16][8-row group row/8][K half (col/8)%2][row%8][col%8],
+// i.e. the canonical K-major layout without swizzle, 8 x 16-byte core
+// matrices, the two K halves 128 bytes apart, row groups 256 bytes apart.
+__host__ __device__ __forceinline__ int64_t slice_elem_off(int64_t row, int col, int64_t rows) {
+  return (int64_t)(col >> 4) * rows * 16 + (row >> 3) * 128 + ((col >> 3) & 1) * 64 + (row & 7) * 8 + (col & 7);
+}
+
 namespace beor {
 
 __host__ __device__ inline int64_t tri_index(int i, int j) { return (int64_t)i * (i + 1) / 2 + j; }

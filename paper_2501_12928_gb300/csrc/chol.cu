@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int kg, int mixe
           X = (X - mm) >> 8;
         }
         dg[0] = (int)X;
-        __nv_bfloat16* dst = v.linv_sl + (part * BEOR_NSLICE * lrows + row) * BEOR_TB + m;
+        __nv_bfloat16* dst = v.linv_sl + part * BEOR_NSLICE * ps + slice_elem_off(row, m, lrows);
 #pragma unroll
         for (int sl = 0; sl < BEOR_NSLICE; ++sl) dst[sl * ps] = __float2bfloat16_rn(ldexpf((float)dg[sl], -8 * sl));
       }

@@ -21,7 +21,8 @@
 //
 // Kernel structure (one CTA per SM, persistent over output tiles of 128 rows
 // x 64 complex columns): warp 0 issues TMA loads of the slice planes into a
-// 3-stage shared-memory ring (32-byte swizzle, K chunks of 16), warp 1 issues
+// 3-stage shared-memory ring (K chunks of 16, stored in global memory in the
+// tensor cores' no-swizzle order and fetched as 512-byte rows), warp 1 issues
 // the tcgen05.mma instructions (M = 128, N = 64..256, K = 16, bf16 -> fp32)
 // into eight TMEM accumulators (4 levels x re/im, all 512 columns), and
 // warps 2-9 (two per TMEM lane quarter, each with half the columns) drain
@@ -59,9 +60,9 @@ constexpr int MX_JOBS = 4;               // depth of the producer -> MMA / epilo
 enum { ERR_TMA_WAIT = 11, ERR_MMA_WAIT = 12, ERR_ACC_WAIT = 13, ERR_EPI_WAIT = 14 };
 
 struct MixedMaps {
-  CUtensorMap panel_a[2];   // panel slices (two buffers by step parity), box 16 x 128 rows x 10 planes
-  CUtensorMap panel_b[2];   // the same, box 16 x 64 rows x 10 planes
-  CUtensorMap linv_b;       // inverse-diagonal slices, box 16 x 64 rows x 10 planes
+  CUtensorMap panel_a[2];   // panel slices (two buffers by step parity), box: 128 rows x one K-chunk x 10 planes
+  CUtensorMap panel_b[2];   // the same, box 64 rows
+  CUtensorMap linv_b;       // inverse-diagonal slices, box 64 rows
   int64_t* d_prefix = nullptr;   // [4][max_nt][P+1] tile prefix sums (kinds col, rest, panel, all)
   int* d_counter = nullptr;      // [4][max_nt] dynamic tile counters, zeroed before every evaluation
   int max_nt = 0, P = 0;
@@ -119,11 +120,11 @@ __device__ __forceinline__ bool mbar_wait_deadline(uint32_t a, uint32_t parity) 
     if ((it & 255u) == 255u && globaltimer() - t0 > MX_TIMEOUT_NS) return false;
   }
 }
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
                                             uint32_t mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(mbar)
       : "memory");
 }
 // Bulk prefetch of a contiguous global range into L2 (size a multiple of 16 bytes).
@@ -181,17 +182,18 @@ __device__ __forceinline__ void reg_fence4(float* v) {
   asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]));
 }
 
-// Shared-memory matrix descriptor: K-major operand, 32-byte swizzle, 8-row
-// groups 256 bytes apart (SBO), leading offset unused (K of one MMA fits the
-// 32-byte swizzle width).
-__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major operand without swizzle, made of
+// 8-row x 16-byte core matrices: the two core matrices of one MMA's K = 16
+// are 128 bytes apart (leading byte offset), 8-row groups 256 bytes apart
+// (stride byte offset).  Every address it yields lies within 256 x (rows / 8)
+// bytes of the start.
+__device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);            // start address
-  d |= (uint64_t)1 << 16;                               // leading byte offset (16 B, unused)
-  d |= (uint64_t)(256 >> 4) << 32;                      // stride byte offset
+  d |= (uint64_t)(128 >> 4) << 16;                      // leading byte offset: next K core matrix
+  d |= (uint64_t)(256 >> 4) << 32;                      // stride byte offset: next 8-row group
   d |= (uint64_t)1 << 46;                               // descriptor version (sm_100 family)
-  d |= (uint64_t)6 << 61;                               // swizzle mode: 32 B
-  return d;
+  return d;                                             // swizzle mode 0: none
 }
 // Instruction descriptor: bf16 x bf16 -> fp32, K-major A and B, M = 128, N given.
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t negate_a, uint32_t n) {
@@ -365,8 +367,9 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           }
           mbar_expect_tx(full_bar(s), MX_STAGE_BYTES);
           const uint32_t dst = sbase + s * MX_STAGE_BYTES;
-          tma_load_3d(dst, &map_a, kc * MX_KC, a_row, 0, full_bar(s));
-          tma_load_3d(dst + MX_A_BYTES, &map_b, kc * MX_KC, b_row, 0, full_bar(s));
+          // x = 0 always (16-byte aligned); y counts pairs of 8-row groups
+          tma_load_4d(dst, &map_a, 0, a_row / 16, kc, 0, full_bar(s));
+          tma_load_4d(dst + MX_A_BYTES, &map_b, 0, b_row / 16, kc, 0, full_bar(s));
         }
       }
     producer_done:
@@ -413,13 +416,13 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           // t = 4 - sa adds into level 3 with N = 64.
 #pragma unroll
           for (int sa = 0; sa < BEOR_NSLICE; ++sa) {
-            const uint64_t ar = sdesc_sw32(a0 + (0 * BEOR_NSLICE + sa) * (MX_M * 32));
-            const uint64_t ai = sdesc_sw32(a0 + (1 * BEOR_NSLICE + sa) * (MX_M * 32));
+            const uint64_t ar = sdesc_kmajor(a0 + (0 * BEOR_NSLICE + sa) * (MX_M * 32));
+            const uint64_t ai = sdesc_kmajor(a0 + (1 * BEOR_NSLICE + sa) * (MX_M * 32));
             const uint32_t acc0 = (kc == 0 && sa == 0) ? 0u : 1u;
             if (sa <= 3) {
               const uint32_t n = (uint32_t)MX_N * (4 - sa);
-              const uint64_t br = sdesc_sw32(b0 + (0 * BEOR_NSLICE + 0) * (MX_N * 32));
-              const uint64_t bi = sdesc_sw32(b0 + (1 * BEOR_NSLICE + 0) * (MX_N * 32));
+              const uint64_t br = sdesc_kmajor(b0 + (0 * BEOR_NSLICE + 0) * (MX_N * 32));
+              const uint64_t bi = sdesc_kmajor(b0 + (1 * BEOR_NSLICE + 0) * (MX_N * 32));
               const uint32_t d_re = tmem + (uint32_t)(sa * MX_N), d_im = tmem + 256u + (uint32_t)(sa * MX_N);
               tc_mma(d_re, ar, br, idesc_bf16(0, n), acc0);
               tc_mma(d_re, ai, bi, idesc_bf16(0, n), 1u);
@@ -428,8 +431,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
             }
             {
               const int tb = 4 - sa;
-              const uint64_t br = sdesc_sw32(b0 + (0 * BEOR_NSLICE + tb) * (MX_N * 32));
-              const uint64_t bi = sdesc_sw32(b0 + (1 * BEOR_NSLICE + tb) * (MX_N * 32));
+              const uint64_t br = sdesc_kmajor(b0 + (0 * BEOR_NSLICE + tb) * (MX_N * 32));
+              const uint64_t bi = sdesc_kmajor(b0 + (1 * BEOR_NSLICE + tb) * (MX_N * 32));
               const uint32_t d_re = tmem + 3u * MX_N, d_im = tmem + 256u + 3u * MX_N;
               tc_mma(d_re, ar, br, idesc_bf16(0, MX_N), 1u);
               tc_mma(d_re, ai, bi, idesc_bf16(0, MX_N), 1u);
@@ -613,7 +616,8 @@ __global__ void __launch_bounds__(256)
         dg[0] = (int)X;
 #pragma unroll
         for (int sl = 0; sl < BEOR_NSLICE; ++sl) {
-          __nv_bfloat16* dst = panel_sl + ((int64_t)(part * BEOR_NSLICE + sl) * rows + grow) * BEOR_TB + lane + 32 * q;
+          __nv_bfloat16* dst = panel_sl + (int64_t)(part * BEOR_NSLICE + sl) * rows * BEOR_TB +
+                               slice_elem_off(grow, lane + 32 * q, rows);
           *dst = __float2bfloat16_rn(ldexpf((float)dg[sl], -8 * sl));
         }
       }
@@ -649,15 +653,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
+// Slice planes in slice_elem_off order seen as a 4-D tensor: 256 elements
+// (two 8-row groups, 512 contiguous bytes) x rows/16 x 8 K-chunks x 10
+// planes.  A box of box_rows rows of one K-chunk of every plane is exactly
+// the shared-memory operand image (no swizzle), fetched as 512-byte rows.
 static cudaError_t make_map(CUtensorMap* m, void* base, int64_t rows, int box_rows) {
   auto enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
-  cuuint64_t dims[3] = {(cuuint64_t)BEOR_TB, (cuuint64_t)rows, (cuuint64_t)BEOR_NPLANE};
-  cuuint64_t strides[2] = {(cuuint64_t)BEOR_TB * 2, (cuuint64_t)rows * BEOR_TB * 2};
-  cuuint32_t box[3] = {(cuuint32_t)MX_KC, (cuuint32_t)box_rows, (cuuint32_t)BEOR_NPLANE};
-  cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  if (rows % 16 || box_rows % 16) return cudaErrorInvalidValue;
+  cuuint64_t dims[4] = {256, (cuuint64_t)(rows / 16), (cuuint64_t)(BEOR_TB / MX_KC), (cuuint64_t)BEOR_NPLANE};
+  cuuint64_t strides[3] = {512, (cuuint64_t)rows * MX_KC * 2, (cuuint64_t)rows * BEOR_TB * 2};
+  cuuint32_t box[4] = {256, (cuuint32_t)(box_rows / 16), 1, (cuuint32_t)BEOR_NPLANE};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
