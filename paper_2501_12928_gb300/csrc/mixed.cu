@@ -586,6 +586,8 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t rows = v.rows;
+  __shared__ int s_e[R];
+  // per-row exponent (one warp per row)
   for (int r = warp; r < R; r += 8) {
     float mx = 0.0f;
 #pragma unroll
@@ -595,11 +597,28 @@ __global__ void __launch_bounds__(256)
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = mx > 0.0f ? ilogbf(mx) + 1 : -1000;
-    const int64_t grow = pr.row_off + (int64_t)i * BEOR_TB + r0 + r;
-    if (lane == 0) panel_exp[grow] = e;
+    if (lane == 0) {
+      s_e[r] = e;
+      panel_exp[pr.row_off + (int64_t)i * BEOR_TB + r0 + r] = e;
+    }
+  }
+  __syncthreads();
+  // Digits.  Each thread makes one 16-byte chunk of every plane: one row and
+  // 8 consecutive columns.  Warp w takes K-chunk w and lane = (8-row group,
+  // K half, row), so that a warp writes 512 contiguous bytes of each plane.
+  static_assert(R == 16 && BEOR_TB / MX_KC == 8, "one warp per K-chunk, 32 chunks of 16 bytes per warp");
+  const int rr = lane & 7, kh = (lane >> 3) & 1, g = lane >> 4;
+  const int r = g * 8 + rr;
+  const int c0 = warp * MX_KC + kh * 8;
+  const int e = s_e[r];
+  const int64_t grow = pr.row_off + (int64_t)i * BEOR_TB + r0 + r;
+  uint32_t packed[BEOR_NPLANE][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float4 a = s[lane + 32 * q][r];
+  for (int q = 0; q < 8; q += 2) {
+    float val[2][BEOR_NPLANE];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float4 a = s[c0 + q + u][r];
 #pragma unroll
       for (int part = 0; part < 2; ++part) {
         const float hi = part ? a.z : a.x, lo = part ? a.w : a.y;
@@ -615,14 +634,20 @@ __global__ void __launch_bounds__(256)
         }
         dg[0] = (int)X;
 #pragma unroll
-        for (int sl = 0; sl < BEOR_NSLICE; ++sl) {
-          __nv_bfloat16* dst = panel_sl + (int64_t)(part * BEOR_NSLICE + sl) * rows * BEOR_TB +
-                               slice_elem_off(grow, lane + 32 * q, rows);
-          *dst = __float2bfloat16_rn(ldexpf((float)dg[sl], -8 * sl));
-        }
+        for (int sl = 0; sl < BEOR_NSLICE; ++sl) val[u][part * BEOR_NSLICE + sl] = ldexpf((float)dg[sl], -8 * sl);
       }
     }
+#pragma unroll
+    for (int pl = 0; pl < BEOR_NPLANE; ++pl) {
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[0][pl], val[1][pl]);   // .x at the lower address
+      packed[pl][q / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+    }
   }
+  const int64_t off = slice_elem_off(grow, c0, rows);   // a multiple of 8 elements: 16-byte aligned
+#pragma unroll
+  for (int pl = 0; pl < BEOR_NPLANE; ++pl)
+    *reinterpret_cast<uint4*>(panel_sl + (int64_t)pl * rows * BEOR_TB + off) =
+        make_uint4(packed[pl][0], packed[pl][1], packed[pl][2], packed[pl][3]);
 }
 
 static __nv_bfloat16* slice_buf(const BatchView& v, int k) {
