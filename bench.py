@@ -159,6 +159,19 @@ def cpu_baseline(insts, n_models, reps=1):
                       f"host cores), scaled to the 6048/7840/11424 mix by (N/{n0})^3"}
 
 
+def workload_config(workload, B, n_models):
+    """The `config` object of the bench line, the same for both arms."""
+    if workload == "c3":
+        name = ("C3: 3 sub-band instruments (n_f 24/32/48, N_model 6048/7840/11424, "
+                "331 baselines x 16 times), B=%d each, one batched evaluation per step" % B)
+    else:
+        name = "C1: one instrument (N_model 3280, 126 baselines x 19 times x 38 channels), B=%d" % B
+    # double-float working matrices: lower-triangle 128-tiles, 16 bytes per complex element
+    ws_bytes = sum(B * (nt * (nt + 1) // 2) * 128 * 128 * 16 for nt in ((n + 127) // 128 for n in n_models))
+    return {"workload": name, "B_per_subband": B, "n_model": list(n_models),
+            "l2": "inputs larger than L2 (working matrices %.1f GB)" % (ws_bytes / 1e9), "parallelism": "replicas"}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -182,7 +195,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "C3 sub-band mix (N_model 6048/7840/11424), oracle sample at N=6048"},
+            "config": workload_config("c3", args.B, n_models),
             "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value,
                              "sample": f"one oracle evaluation at N_model={inst.spec.n_model} per step, "
                                        "scaled to the mix by (N/6048)^3"},
@@ -352,12 +365,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16 slice products (exact, fp32 accumulate) + double-float / f64",
             "data": "synthetic",
-            "config": {"workload": ("C3: 3 sub-band instruments (n_f 24/32/48, N_model 6048/7840/11424, "
-                                    "331 baselines x 16 times), B=%d each, one batched evaluation per step" % args.B)
-                       if args.workload == "c3" else
-                       "C1: one instrument (N_model 3280, 126 baselines x 19 times x 38 channels), B=%d" % args.B,
-                       "B_per_subband": args.B, "n_model": n_models, "precompute_s": round(t_pre, 2),
-                       "l2": "inputs larger than L2 (working matrices ~30 GB)", "parallelism": "replicas"},
+            "config": dict(workload_config(args.workload, args.B, n_models), precompute_s=round(t_pre, 2)),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * sum(p.size for p in host_phi),
                     "d2h_bytes_per_step": 12 * evals_step},
             "gpu_launches": int(launches) * args.steps,
