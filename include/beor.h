@@ -108,7 +108,19 @@ int beor_precompute(beor_ctx *ctx, void *stream);
 /* lnL for B prior points.  phi: B x n_k float64, row-major, log10 power
  * amplitudes (host or device).  lnl_out: B float64, status_out: B int32
  * (host or device).  The whole batch is factorised together; the call
- * returns after the results are written.
+ * returns after the results are written.  1 <= B <= 4096 (BEOR_EINVAL
+ * otherwise, including an empty batch); non-finite phi in host memory is
+ * BEOR_EINVAL.
+ * Workspaces: the first call for a batch shape (its contexts and their B;
+ * lnL, posterior mean and each asynchronous slot count separately)
+ * allocates that batch's device workspaces -- per point the packed lower
+ * triangle of Sigma at 16 bytes per complex element (about 92 MB at
+ * n_model = 3280, 1.07 GB at 11,424) plus bf16 slices and vectors -- and
+ * captures its CUDA graph (BEOR_ENOMEM if they do not fit).  Both are kept
+ * for later calls of the same shape and released when one of its contexts
+ * is re-set (beor_set_T, beor_set_instrument, beor_set_data,
+ * beor_precompute) or destroyed, so callers with varying B should use a
+ * few sizes (e.g. pad to powers of two).
  * Mixed precision: the quadratic form q = dbar^H Sigma^-1 dbar is evaluated
  * from the first solution x~ of the approximate factor L~ and one float64
  * residual r = dbar - Sigma x~ as q = dbar^H x~ + x~^H r + |L~^-1 r|^2
