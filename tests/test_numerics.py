@@ -8,6 +8,11 @@
   residuals), as the bf16 slicing does.
 * Dot2 (Ogita, Rump and Oishi 2005) in float32 reaches about twice the
   working precision, as the solves and the residual rely on.
+* The bf16 slicing: five balanced base-256 digits reconstruct any
+  fixed-point value |X| <= 2^39 exactly, each slice is exact in bf16, the
+  float32 level accumulators of levels 0-2 are exact over a 128-complex
+  block column, and the four levels give the product to about 2^-40 of the
+  operand row scales.
 """
 
 import numpy as np
@@ -83,3 +88,67 @@ def test_dot2_reaches_twice_the_working_precision():
     u = 2.0 ** -24
     assert abs(d2 - exact) <= u * abs(exact) + 2 * (n * u) ** 2 * cond
     assert abs(d2 - exact) < abs(plain - exact) * 1e-3 or abs(plain - exact) == 0
+
+
+def _digits5(X):
+    """Five balanced base-256 digits of integers |X| <= 2^39, as the bf16
+    slicing forms them: X = sum_s d_s 256^(4 - s), |d_s| <= 128."""
+    X = np.asarray(X, np.int64).copy()
+    d = np.zeros((5,) + X.shape, np.int64)
+    for s in range(4, 0, -1):
+        m = ((X + 128) & 255) - 128
+        d[s] = m
+        X = (X - m) >> 8
+    d[0] = X
+    return d
+
+
+def test_balanced_digits_reconstruct_and_are_exact_in_bf16():
+    g = np.random.default_rng(3)
+    edge = [2 ** 39, -2 ** 39, 2 ** 39 - 1, 0, 127, 128, -128, -129, 255 * 2 ** 31]
+    X = np.concatenate([g.integers(-2 ** 39, 2 ** 39, 200_000), edge])
+    d = _digits5(X)
+    rec = sum(d[s] * 256 ** (4 - s) for s in range(5))
+    assert np.array_equal(rec, X)
+    assert np.abs(d).max() <= 128
+    for s in range(5):
+        v = (d[s] * 2.0 ** (-8 * s)).astype(np.float32)
+        assert np.all((v.view(np.uint32) & 0xFFFF) == 0)   # bf16 keeps the top 16 bits of a float32
+
+
+def test_slice_product_levels_exact_and_sum_accurate():
+    """One 128-complex block column (K = 256 real terms per output) as the
+    trailing update computes it: rows scaled by 2^(39 - e) and split into
+    digits, the 15 slice pairs with s + t <= 4 accumulated in float32 in
+    four level accumulators (pairs with s + t >= 3 share the last).  Levels
+    0-2 are exact; the four levels scaled by 2^(e_a + e_b - 14) give A B^T to
+    about 2^-40 of the row scales."""
+    g = np.random.default_rng(4)
+    K, m, n = 256, 48, 24
+    A = g.standard_normal((m, K)) * np.exp(g.uniform(-3, 3, (m, 1)))
+    B = g.standard_normal((n, K)) * np.exp(g.uniform(-3, 3, (n, 1)))
+
+    def fixed(M):
+        e = np.floor(np.log2(np.abs(M).max(axis=1))).astype(np.int64) + 1   # |row| < 2^e
+        return np.rint(M * np.exp2(39 - e)[:, None]).astype(np.int64), e
+
+    XA, eA = fixed(A)
+    XB, eB = fixed(B)
+    dA, dB = _digits5(XA), _digits5(XB)
+    lev = np.zeros((4, m, n), np.float32)
+    exact = np.zeros((3, m, n), np.int64)          # levels 0-2 in units of 2^(-8 l)
+    for s in range(5):
+        for t in range(5 - s):
+            l = min(s + t, 3)
+            a = (dA[s] * 2.0 ** (-8 * s)).astype(np.float32)
+            b = (dB[t] * 2.0 ** (-8 * t)).astype(np.float32)
+            for k in range(K):                      # sequential float32 accumulation
+                lev[l] += np.outer(a[:, k], b[:, k])
+            if l < 3:
+                exact[l] += dA[s] @ dB[t].T
+    for l in range(3):
+        assert np.array_equal(lev[l].astype(np.float64) * 2.0 ** (8 * l), exact[l].astype(np.float64)), l
+    P = lev.astype(np.float64).sum(axis=0) * np.exp2(eA[:, None] + eB[None, :] - 14)
+    scale = K * np.exp2(eA[:, None] + eB[None, :])
+    err = np.abs(P - A @ B.T) / scale
+    assert err.max() <= 2.0 ** -40, err.max()          # measured: 2^-42.4
