@@ -13,6 +13,7 @@
   float32 level accumulators of levels 0-2 are exact over a 128-complex
   block column, and the four levels give the product to about 2^-40 of the
   operand row scales.
+* The residual's exact split of M into three floats per component.
 """
 
 import numpy as np
@@ -152,3 +153,20 @@ def test_slice_product_levels_exact_and_sum_accurate():
     scale = K * np.exp2(eA[:, None] + eB[None, :])
     err = np.abs(P - A @ B.T) / scale
     assert err.max() <= 2.0 ** -40, err.max()          # measured: 2^-42.4
+
+
+def test_float_triple_split_of_m_is_exact():
+    """The residual reads M as three floats per component: hi = fl(m),
+    lo = fl(m - hi), t = fl(m - hi - lo).  Both remainders are exact in
+    float64 and the last has at most 53 - 48 significant bits, so
+    hi + lo + t == m exactly (for magnitudes far above float32's underflow,
+    as M's entries are)."""
+    g = np.random.default_rng(5)
+    m = g.standard_normal(200_000) * np.exp(g.uniform(np.log(1e-6), np.log(1e7), 200_000))
+    hi = m.astype(np.float32)
+    rd = m - hi.astype(np.float64)
+    lo = rd.astype(np.float32)
+    t = (rd - lo.astype(np.float64)).astype(np.float32)
+    assert np.array_equal((hi.astype(np.float64) + lo.astype(np.float64)) + t.astype(np.float64), m)
+    assert np.all(np.abs(lo.astype(np.float64)) <= np.spacing(np.abs(hi)).astype(np.float64) / 2)
+    assert np.all(np.abs(t.astype(np.float64)) <= np.spacing(np.abs(lo)).astype(np.float64) / 2)
