@@ -207,7 +207,10 @@ int beor_get_terms(const beor_ctx *ctx, double *logdet_phi, double *logdet_sigma
 
 /* Cholesky factor L (n_model x n_model, lower, row-major, host memory) of
  * prior point b of the last beor_lnl call on ctx, as left in the working
- * matrix by the factorisation (diagnostics and tests). */
+ * matrix by the factorisation (diagnostics and tests).
+ * Both read the last batch's workspaces: once any context of that batch is
+ * re-set or destroyed, beor_get_terms returns BEOR_ESTATE and
+ * beor_get_factor BEOR_EINVAL until the next evaluation. */
 int beor_get_factor(const beor_ctx *ctx, int b, beor_c128 *L_out);
 
 /* dbar = T^H N^-1 d of a factored instrument (same arguments and result as

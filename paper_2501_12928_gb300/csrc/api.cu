@@ -460,10 +460,16 @@ void drop_plans_of(beor_ctx* c) {
   std::lock_guard<std::mutex> lk(g_mu);
   std::vector<Plan*> keep;
   for (Plan* p : g_plans) {
-    if (std::find(p->ctxs.begin(), p->ctxs.end(), c) != p->ctxs.end())
+    if (std::find(p->ctxs.begin(), p->ctxs.end(), c) != p->ctxs.end()) {
+      // the other contexts of a multi-context batch may still name this plan
+      // as their last one (diagnostics); every context in a kept plan is
+      // alive, since destroying a context drops its plans first
+      for (beor_ctx* o : p->ctxs)
+        if (o->last_plan == p) o->last_plan = nullptr;
       delete p;
-    else
+    } else {
       keep.push_back(p);
+    }
   }
   g_plans.swap(keep);
 }
