@@ -71,8 +71,11 @@ enum { BEOR_PREC_FP64 = 0, BEOR_PREC_MIXED = 1 };
  * precision = BEOR_PREC_MIXED: trailing and panel updates of the blocked
  *   Cholesky run as exact bf16 slice products on the tensor cores with fp32
  *   accumulation, the working matrix is kept as a pair of fp32 words per
- *   real number, diagonal blocks and log-determinants in float64, and the
- *   solve is refined against the float64 precompute. */
+ *   real number, the diagonal-block Cholesky factorisations and the
+ *   log-determinants are float64 (the blocks' inverses are formed on the
+ *   fp32 pipe to ~2^-48), and a float64-accurate residual against the
+ *   float64 precompute corrects the quadratic form (lnL) or refines the
+ *   solution (posterior mean). */
 int beor_create(beor_ctx **out, int device, int precision);
 int beor_destroy(beor_ctx *ctx);
 
