@@ -1,7 +1,9 @@
-"""The benchmark's clock record, from nvidia-smi rows sampled during the
-timed region: median SM clock, maximum clock, and every throttle reason
-seen active (a run with a hardware or thermal slowdown is not a valid
-measurement; sw_power_cap is kept and noted)."""
+"""Host-side pieces of the benchmark line: the clock record, from
+nvidia-smi rows sampled during the timed region (median SM clock, maximum
+clock, and every throttle reason seen active; a run with a hardware or
+thermal slowdown is not a valid measurement, sw_power_cap is kept and
+noted), and the roofline's DRAM traffic read from the committed ncu
+summary."""
 
 from bench import ClockSampler
 
@@ -24,3 +26,13 @@ def test_summary_median_max_and_reasons():
 def test_summary_without_samples():
     s = ClockSampler(0).summary()
     assert s["sm_mhz"] is None and s["reasons"] == ["no samples"]
+
+
+def test_traffic_comes_from_the_committed_profile():
+    """roofline.traffic is the trailing kernel's ncu DRAM bytes per tile
+    (profiles/slice_gemm_trail_C1_B8.md) times the tiles of a launch."""
+    from bench import _traffic_per_launch
+    per_tile = _traffic_per_launch(1.0)
+    assert per_tile is not None
+    # the working matrix's read and write: 128 x 64 complex double-float = 262 KB
+    assert 262_144 <= per_tile <= 1.05 * 262_144
