@@ -40,7 +40,10 @@
  *    outside its tolerance (lnL still returned): for beor_lnl /
  *    beor_lnl_multi, the estimated error of the residual-corrected
  *    quadratic form is above 1e-2; for beor_posterior_mean, the last
- *    iterative-refinement correction is above 1e-4 of the solution.
+ *    iterative-refinement correction is above 1e-4 of the solution;
+ *    -2 = the point's phi (passed in device memory) is not finite: the
+ *    point is skipped and its lnL is NaN (phi in host memory is checked
+ *    before launch instead, BEOR_EINVAL).
  */
 #ifndef BEOR_H
 #define BEOR_H
@@ -183,6 +186,9 @@ typedef struct {
   int64_t kernel_launches;  /* kernels launched by the last batched evaluation */
   double ms_class[8];
   int64_t n_class[8];
+  int32_t device_error;     /* after BEOR_ETIMEOUT: the bounded wait that gave up first (11 copy
+                               producer, 12 tensor-core issuer waiting for operands, 13 issuer
+                               waiting for the accumulators, 14 epilogue); 0 otherwise */
 } beor_stats;
 int beor_get_stats(const beor_ctx *ctx, beor_stats *out);
 
@@ -202,6 +208,20 @@ int beor_set_profiling(int on);
  * Off: one stream, steps in order.
  * Float64 contexts always use the in-order schedule. */
 int beor_set_lookahead(int on);
+
+/* Test hook of the failure detection of the tensor-core kernels (process
+ * wide, off by default: beor_set_wait_test(0, 0)).  Each role of those
+ * kernels (copy producer, tensor-core issuer, epilogue) waits on the others
+ * with a bounded wait; when one gives up, the kernel records which wait it
+ * was, drains the copies and tensor-core work it issued, releases its
+ * tensor memory and returns, and the call reports BEOR_ETIMEOUT (the
+ * context is then poisoned).  limit_ms > 0 sets the role-wait limit
+ * (0 = the default 2000 ms; the drain keeps its own 2 s limit);
+ * skip_one_copy != 0 makes the first trailing-update CTA of the next
+ * evaluations withhold one operand copy, so that the issuer's wait for it
+ * can only end by the limit.  Graphs captured with other settings are
+ * rebuilt on their next use.  BEOR_EINVAL for limit_ms < 0 or > 60000. */
+int beor_set_wait_test(int skip_one_copy, double limit_ms);
 
 /* Per-point log-determinant pieces of the last beor_lnl call on ctx (B
  * values each, host memory): log|Phi|, log|Sigma| and q = dbar^H abar. */
@@ -223,8 +243,9 @@ int beor_get_factor(const beor_ctx *ctx, int b, beor_c128 *L_out);
  * loop that must never stall on cudaMalloc / cudaFree.  This call allocates
  * nothing: the per-frequency partial sums live in a fixed 1 MiB device
  * array built into the library, so it needs nf * ncells <= 65536 and
- * returns BEOR_EINVAL beyond that.  All pointers must be device memory
- * (BEOR_EINVAL otherwise): A nf x ntb x ncells, W nf x nx, noise_var and d
+ * returns BEOR_EINVAL beyond that.  All pointers must be memory of the
+ * current device, or managed memory (BEOR_EINVAL otherwise, host memory and
+ * other GPUs' memory included): A nf x ntb x ncells, W nf x nx, noise_var and d
  * nf*ntb, dbar_out ncells*nx.  The work is enqueued on `stream`; dbar_out
  * is valid when the stream reaches it.  The first call on a device looks up
  * the array's device address (make that first call before any stream
@@ -237,9 +258,18 @@ int beor_dbar_factored_noalloc(const beor_c128 *A, const beor_c128 *W, int nf, i
 
 /* ---------------------------------------------------------------------
  * Learned emulator of lnL(phi) (pre-screening for the nested sampler).
+ * The paper samples phi with nested sampling (Sec. "Summary": MultiNest,
+ * with the evidence used for model selection); this emulator is an
+ * addition of this library that the paper does not have: it only screens
+ * candidate points, while every accepted point and the evidence use the
+ * exact likelihood above.
  * A multilayer perceptron n_in -> depth x width GELU -> 1 with bf16 weights
  * and activations, fp32 accumulation and fp32 master weights / Adam state,
- * trained and evaluated by the library's own kernels.
+ * trained and evaluated by the library's own kernels.  Inputs and targets
+ * are float32 (the network's own precision; callers convert the float64
+ * phi and lnL), and training is one Adam step per call
+ * (beor_mlp_train_step) so that the caller owns the epoch loop, the
+ * minibatch order and the learning-rate schedule.
  * ------------------------------------------------------------------- */
 typedef struct beor_mlp beor_mlp;
 

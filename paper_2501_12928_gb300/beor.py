@@ -53,6 +53,7 @@ def _load():
         "beor_get_factor": [_P, _c.c_int, _P],
         "beor_set_profiling": [_c.c_int],
         "beor_set_lookahead": [_c.c_int],
+        "beor_set_wait_test": [_c.c_int, _c.c_double],
         "beor_dbar_factored_noalloc": [_P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _P, _P, _P, _P],
         "beor_mlp_create": [_c.POINTER(_P), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64],
         "beor_mlp_destroy": [_P],
@@ -91,7 +92,8 @@ def _check(code, what):
 class _Stats(ctypes.Structure):
     _fields_ = [("refine_iters_max", ctypes.c_int), ("resid_rel_max", ctypes.c_double),
                 ("ms_last", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("ms_class", ctypes.c_double * 8), ("n_class", ctypes.c_int64 * 8)]
+                ("ms_class", ctypes.c_double * 8), ("n_class", ctypes.c_int64 * 8),
+                ("device_error", ctypes.c_int32)]
 
 
 KERNEL_CLASSES = ("init", "diag", "slice", "panel", "trail", "solve", "refine", "lnl")
@@ -103,6 +105,11 @@ def set_profiling(on: bool):
 
 def set_lookahead(on: bool):
     _check(_lib().beor_set_lookahead(1 if on else 0), "beor_set_lookahead")
+
+
+def set_wait_test(skip_one_copy: bool, limit_ms: float = 0.0):
+    """Failure-detection test hook (see beor_set_wait_test); (False, 0) is the default."""
+    _check(_lib().beor_set_wait_test(1 if skip_one_copy else 0, float(limit_ms)), "beor_set_wait_test")
 
 
 def _stream(stream):
@@ -229,6 +236,7 @@ class Likelihood:
         out = {k: getattr(st, k) for k, _ in st._fields_[:4]}
         out["ms_class"] = dict(zip(KERNEL_CLASSES, list(st.ms_class)))
         out["n_class"] = dict(zip(KERNEL_CLASSES, list(st.n_class)))
+        out["device_error"] = st.device_error
         return out
 
     def factor(self, b: int = 0):

@@ -23,6 +23,10 @@ constexpr int kClasses = 8;       // kernel classes timed when profiling is on
 enum { KC_INIT = 0, KC_DIAG, KC_SLICE, KC_PANEL, KC_TRAIL, KC_SOLVE, KC_REFINE, KC_LNL };
 bool g_profiling = false;
 bool g_lookahead = true;
+// bounded-wait test switch (beor_set_wait_test): role-wait limit (0 = the
+// kernels' own 2 s) and whether one operand copy is withheld
+unsigned long long g_wait_ns = 0;
+int g_skip_copy = 0;
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -124,6 +128,8 @@ struct Plan {
   bool refine_x = false;            // mixed: refine the solution (posterior mean) rather than correct q
   int slot = 0;                     // independent copies of one batch shape (asynchronous calls)
   bool lookahead = true;            // schedule of the mixed factorisation captured in the graph
+  unsigned long long wait_ns = 0;   // bounded-wait settings captured in the graph
+  int skip_copy = 0;
   int prio_hi = 0;                  // greatest stream priority of the device
   std::vector<cudaEvent_t> pev;     // boundary events (profiling)
   std::vector<int> pcls;            // class of the launch after each boundary event
@@ -715,6 +721,10 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
     // first use: run once directly (sets kernel attributes), then capture
     int64_t nl = 0;
     pl->lookahead = g_lookahead;
+    pl->wait_ns = g_wait_ns;
+    pl->skip_copy = g_skip_copy;
+    pl->view.wait_ns = g_wait_ns;
+    pl->view.test_skip_copy = g_skip_copy;
     CKC(c0, run_sequence(*pl, st, &nl, false));
     pl->launches = nl;
     CKC(c0, cudaStreamSynchronize(st));
@@ -753,7 +763,10 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
     int err = 0;
     CKC(c0, cudaMemcpy(&err, &pl->view.flags->error, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
-      for (int s = 0; s < nsets; ++s) ctxs[s]->poisoned = true;
+      for (int s = 0; s < nsets; ++s) {
+        ctxs[s]->poisoned = true;
+        ctxs[s]->stats.device_error = err;
+      }
       return BEOR_ETIMEOUT;
     }
   }
@@ -782,6 +795,7 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
   for (int s = 0; s < nsets; ++s) {
     beor_ctx* c = ctxs[s];
     c->stats.ms_last = ms;
+    c->stats.device_error = 0;
     c->stats.kernel_launches = pl->launches;
     c->stats.refine_iters_max = pl->mixed && pl->refine_x ? kRefineIters : 0;
     double mx = 0.0;
@@ -822,7 +836,10 @@ int beor_lnl_multi_wait(beor_ctx* const* ctxs, int nsets, const int* B, int slot
   int err = 0;
   CKC(c0, cudaMemcpy(&err, &pl->view.flags->error, sizeof(int), cudaMemcpyDeviceToHost));
   if (err) {
-    for (int s = 0; s < nsets; ++s) ctxs[s]->poisoned = true;
+    for (int s = 0; s < nsets; ++s) {
+      ctxs[s]->poisoned = true;
+      ctxs[s]->stats.device_error = err;
+    }
     return BEOR_ETIMEOUT;
   }
   return BEOR_OK;
@@ -900,7 +917,9 @@ int beor_get_dbar(beor_ctx* c, beor_c128* out) {
 // graphs captured with another setting are rebuilt on their next use
 static void drop_stale_graphs() {
   for (Plan* p : g_plans) {
-    if ((p->prof != g_profiling || p->lookahead != g_lookahead) && p->exec) {
+    if ((p->prof != g_profiling || p->lookahead != g_lookahead || p->wait_ns != g_wait_ns ||
+         p->skip_copy != g_skip_copy) &&
+        p->exec) {
       cudaGraphExecDestroy(p->exec);
       cudaGraphDestroy(p->graph);
       p->exec = nullptr;
@@ -919,6 +938,15 @@ int beor_set_profiling(int on) {
 int beor_set_lookahead(int on) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_lookahead = on != 0;
+  drop_stale_graphs();
+  return BEOR_OK;
+}
+
+int beor_set_wait_test(int skip_one_copy, double limit_ms) {
+  if (!(limit_ms >= 0.0) || limit_ms > 60000.0) return BEOR_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_skip_copy = skip_one_copy != 0;
+  g_wait_ns = (unsigned long long)(limit_ms * 1e6);
   drop_stale_graphs();
   return BEOR_OK;
 }

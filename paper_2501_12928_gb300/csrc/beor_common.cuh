@@ -75,6 +75,13 @@ struct Flags {
   int pad[31];
 };
 
+// Per-problem status values besides 0 (ok), j > 0 (not positive definite at
+// column j) and -1 (result outside its tolerance estimate, set at the end):
+// -2 marks a prior point with a non-finite phi, found when the prior is
+// formed; such a problem is skipped by every later kernel.
+constexpr int STATUS_BAD_PHI = -2;
+__host__ __device__ __forceinline__ bool prob_skipped(int st) { return st > 0 || st == STATUS_BAD_PHI; }
+
 // ---------------------------------------------------------------------------
 // double-float helpers (Dekker / Knuth error-free transformations, FMA based)
 // ---------------------------------------------------------------------------

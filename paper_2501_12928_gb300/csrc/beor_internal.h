@@ -56,6 +56,12 @@ struct BatchView {
   const RWork* rwork;        // CTA work items
   int n_rwork;
   int64_t rows;              // sum of padded dimensions
+  // bounded waits of the tensor-core kernels: limit of a role's wait on
+  // another role (ns), and a test switch (nonzero: the first trailing-update
+  // CTA of the evaluation withholds one operand copy, so that the wait on it
+  // runs out and the error path is taken)
+  unsigned long long wait_ns;
+  int test_skip_copy;
 };
 
 // Launch with an explicit scheduling priority (0: the stream's own); the

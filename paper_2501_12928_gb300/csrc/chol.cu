@@ -66,6 +66,13 @@ __global__ void prior_kernel(BatchView v) {
   const double* phi = sd.phi + (int64_t)pr.b * sd.n_k;
   const double ln10 = 2.302585092994045684;
   __shared__ double red[33];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  // a non-finite phi (possible only for device-memory input, which the host
+  // does not read) marks the point; every later kernel skips it
+  for (int i = threadIdx.x; i < sd.n_k; i += blockDim.x)
+    if (!isfinite(phi[i])) s_bad = 1;
   double acc = 0.0;
   const int np = pr.nt * BEOR_TB;
   for (int j = threadIdx.x; j < np; j += blockDim.x) {
@@ -83,11 +90,11 @@ __global__ void prior_kernel(BatchView v) {
     }
     v.phi_inv[pr.row_off + j] = inv;
   }
-  double tot = block_sum(acc, red);
+  double tot = block_sum(acc, red);   // its barriers also order the writes of s_bad
   if (threadIdx.x == 0) {
     v.logdet_phi[p] = tot;
     v.logdet_sigma[p] = 0.0;
-    v.status[p] = 0;
+    v.status[p] = s_bad ? STATUS_BAD_PHI : 0;
     v.resid[p] = 0.0;
   }
 }
@@ -693,7 +700,7 @@ __global__ void __launch_bounds__(256) fwd_step_kernel(BatchView v, int kg, cons
   const int k = kg - pr.k_off;   // this problem's step (-1: start)
   if (k < -1) return;
   const int i = k + 1 + blockIdx.x;
-  if (i >= pr.nt || v.status[p] > 0) return;
+  if (i >= pr.nt || prob_skipped(v.status[p])) return;
   const int tid = threadIdx.x;
   double2* r = v.vec_t + pr.row_off;
   double2* y = v.vec_y + pr.row_off;
@@ -752,7 +759,7 @@ __global__ void __launch_bounds__(256) bwd_step_kernel(BatchView v, int k, doubl
   __shared__ double2 rk[BEOR_TB];
   const int p = blockIdx.y;
   const Prob pr = v.prob[p];
-  if (v.status[p] > 0) return;
+  if (prob_skipped(v.status[p])) return;
   const int tid = threadIdx.x;
   double2* r = v.vec_t + pr.row_off;
   double2* x = out + pr.row_off;
@@ -905,7 +912,9 @@ __global__ void lnl_kernel(BatchView v, int corr) {
       if (v.status[p] == 0 && !(eta * t <= 1e-2)) v.status[p] = -1;
     }
     v.q[p] = q;
-    if (v.status[p] > 0)
+    if (v.status[p] == STATUS_BAD_PHI)
+      v.lnl[p] = __longlong_as_double(0x7ff8000000000000ll);   // NaN: no likelihood for a non-finite phi
+    else if (v.status[p] > 0)
       v.lnl[p] = -INFINITY;
     else
       v.lnl[p] = -0.5 * v.logdet_phi[p] - 0.5 * v.logdet_sigma[p] + 0.5 * q;

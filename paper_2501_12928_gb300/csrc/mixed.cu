@@ -51,7 +51,7 @@ constexpr int MX_SMEM = MX_STAGES * MX_STAGE_BYTES + 1024 + 256;
 constexpr int MX_EPI_WARPS = 8;        // two warps per TMEM lane quarter, each draining half the columns
 constexpr int MX_THREADS = 64 + 32 * MX_EPI_WARPS;
 constexpr uint32_t MX_TMEM_COLS = 512;
-constexpr unsigned long long MX_TIMEOUT_NS = 2000000000ull;
+constexpr unsigned long long MX_TIMEOUT_NS = 2000000000ull;   // draining this CTA's own copies and MMAs
 
 enum { MODE_TRAIL = 0, MODE_PANEL = 1 };
 // trailing tiles of block step k: the next block column (j = k + 1) or the rest (j >= k + 2)
@@ -100,15 +100,17 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false when the deadline passed or another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait of one role on another: false when `limit_ns` passed or
+// another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit_ns) {
   if (mbar_try(a, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try(a, parity)) return true;
     if ((it & 255u) == 255u) {
       if (*abort_flag) return false;
-      if (globaltimer() - t0 > MX_TIMEOUT_NS) return false;
+      if (globaltimer() - t0 > limit_ns) return false;
     }
   }
 }
@@ -243,7 +245,7 @@ __device__ __forceinline__ bool decode_tile(const BatchView& v, const int64_t* p
   }
   const int p = lo;
   int64_t u = t - prefix[p];
-  if (v.status[p] > 0) return false;
+  if (prob_skipped(v.status[p])) return false;
   k -= v.prob[p].k_off;   // this problem's block step
   jb.p = p;
   jb.h = (int)(u % (BEOR_TB / MX_N));
@@ -278,6 +280,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 18);
   TileJob* jobs = reinterpret_cast<TileJob*>(bars + 20);   // MX_JOBS slots
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long wait_ns = v.wait_ns ? v.wait_ns : MX_TIMEOUT_NS;
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
@@ -330,10 +333,11 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     // to the MMA and epilogue warps through a ring of MX_JOBS slots.
     if (lane == 0) {
       uint32_t it = 0;
+      uint32_t withheld = ~0u;   // iteration whose copy the test switch withheld (never waited for)
       for (uint32_t n = 0;; ++n) {
         const uint32_t q = n % MX_JOBS;
-        if (!mbar_wait(job_empty(q), ((n / MX_JOBS) & 1) ^ 1, abort_flag)) {
-          atomicExch(&v.flags->error, ERR_TMA_WAIT);
+        if (!mbar_wait(job_empty(q), ((n / MX_JOBS) & 1) ^ 1, abort_flag, wait_ns)) {
+          atomicCAS(&v.flags->error, 0, ERR_TMA_WAIT);
           *abort_flag = 1;
           goto producer_done;
         }
@@ -360,10 +364,16 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         for (int kc = 0; kc < BEOR_TB / MX_KC; ++kc, ++it) {
           const int s = it % MX_STAGES;
           const uint32_t ph = (it / MX_STAGES) & 1;
-          if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag)) {
-            atomicExch(&v.flags->error, ERR_TMA_WAIT);
+          if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag, wait_ns)) {
+            atomicCAS(&v.flags->error, 0, ERR_TMA_WAIT);
             *abort_flag = 1;
             goto producer_done;
+          }
+          if (MODE == MODE_TRAIL && v.test_skip_copy && blockIdx.x == 0 && n == 0 && kc == 3) {
+            // test switch: no copy and no arrival for this stage, so the MMA
+            // warp's wait on it can only end by its limit
+            withheld = it;
+            continue;
           }
           mbar_expect_tx(full_bar(s), MX_STAGE_BYTES);
           const uint32_t dst = sbase + s * MX_STAGE_BYTES;
@@ -375,7 +385,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     producer_done:
       // drain: every issued copy must have landed before the CTA may exit
       for (uint32_t q = (it >= MX_STAGES ? it - MX_STAGES : 0); q < it; ++q)
-        mbar_wait_deadline(full_bar(q % MX_STAGES), (q / MX_STAGES) & 1);
+        if (q != withheld) mbar_wait_deadline(full_bar(q % MX_STAGES), (q / MX_STAGES) & 1);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -383,16 +393,16 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       uint32_t it = 0, tcount = 0;
       for (uint32_t n = 0;; ++n) {
         const uint32_t q = n % MX_JOBS;
-        if (!mbar_wait(job_full(q), (n / MX_JOBS) & 1, abort_flag)) {
-          atomicExch(&v.flags->error, ERR_MMA_WAIT);
+        if (!mbar_wait(job_full(q), (n / MX_JOBS) & 1, abort_flag, wait_ns)) {
+          atomicCAS(&v.flags->error, 0, ERR_MMA_WAIT);
           *abort_flag = 1;
           break;
         }
         const TileJob jb = jobs[q];
         mbar_arrive(job_empty(q));
         if (jb.p < 0) break;
-        if (!mbar_wait(acc_empty, (tcount & 1) ^ 1, abort_flag)) {
-          atomicExch(&v.flags->error, ERR_ACC_WAIT);
+        if (!mbar_wait(acc_empty, (tcount & 1) ^ 1, abort_flag, wait_ns)) {
+          atomicCAS(&v.flags->error, 0, ERR_ACC_WAIT);
           *abort_flag = 1;
           break;
         }
@@ -401,8 +411,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         for (int kc = 0; kc < BEOR_TB / MX_KC; ++kc, ++it) {
           const int s = it % MX_STAGES;
           const uint32_t ph = (it / MX_STAGES) & 1;
-          if (!mbar_wait(full_bar(s), ph, abort_flag)) {
-            atomicExch(&v.flags->error, ERR_MMA_WAIT);
+          if (!mbar_wait(full_bar(s), ph, abort_flag, wait_ns)) {
+            atomicCAS(&v.flags->error, 0, ERR_MMA_WAIT);
             *abort_flag = 1;
             bad = true;
             break;
@@ -458,8 +468,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     uint32_t tcount = 0;
     for (uint32_t n = 0;; ++n) {
       const uint32_t q = n % MX_JOBS;
-      if (!mbar_wait(job_full(q), (n / MX_JOBS) & 1, abort_flag)) {
-        atomicExch(&v.flags->error, ERR_EPI_WAIT);
+      if (!mbar_wait(job_full(q), (n / MX_JOBS) & 1, abort_flag, wait_ns)) {
+        atomicCAS(&v.flags->error, 0, ERR_EPI_WAIT);
         *abort_flag = 1;
         break;
       }
@@ -483,8 +493,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 #pragma unroll
         for (int q = 0; q < EC; ++q) cv[q] = __ldcs(C + (int64_t)(cbeg + q) * BEOR_TB);
       }
-      if (!mbar_wait(acc_full, tcount & 1, abort_flag)) {
-        atomicExch(&v.flags->error, ERR_EPI_WAIT);
+      if (!mbar_wait(acc_full, tcount & 1, abort_flag, wait_ns)) {
+        atomicCAS(&v.flags->error, 0, ERR_EPI_WAIT);
         *abort_flag = 1;
         break;
       }
@@ -576,7 +586,7 @@ __global__ void __launch_bounds__(256)
   const Prob pr = v.prob[p];
   const int k = kg - pr.k_off;   // this problem's block step
   const int i = k + 1 + blockIdx.x / (BEOR_TB / R);
-  if (k < 0 || i >= pr.nt || v.status[p] > 0) return;
+  if (k < 0 || i >= pr.nt || prob_skipped(v.status[p])) return;
   const int r0 = (blockIdx.x % (BEOR_TB / R)) * R;
   const float4* tile = reinterpret_cast<const float4*>(v.ws) + pr.ws_off + tri_index(i, k) * BEOR_TILE_ELEMS;
   for (int e = threadIdx.x; e < BEOR_TB * R; e += 256) {
@@ -869,7 +879,7 @@ __global__ void __launch_bounds__(256, 2) resid_df_kernel(BatchView v) {
   const int r = threadIdx.x & (BEOR_TB - 1), half = threadIdx.x >> 7;
   if (threadIdx.x < RG) {
     const int q = threadIdx.x;
-    roff[q] = q < w.nb && v.status[w.p0 + q] <= 0 ? v.prob[w.p0 + q].row_off : (int64_t)-1;
+    roff[q] = q < w.nb && !prob_skipped(v.status[w.p0 + q]) ? v.prob[w.p0 + q].row_off : (int64_t)-1;
   }
   double tre[8], tim[8];
 #pragma unroll
@@ -971,7 +981,7 @@ cudaError_t launch_residual(const BatchView& v, cudaStream_t s) {
 __global__ void refine_update_kernel(BatchView v) {
   const int p = blockIdx.x;
   const Prob pr = v.prob[p];
-  if (v.status[p] > 0) return;
+  if (prob_skipped(v.status[p])) return;
   __shared__ double red[2][32];
   const int np = pr.nt * BEOR_TB;
   double a = 0.0, b = 0.0;

@@ -94,13 +94,17 @@ int noalloc_scratch(double2** out) {
   return BEOR_OK;
 }
 
-bool on_device(const void* p) {
+// Device memory of device `dev` (the current one), or managed memory: a
+// pointer to another GPU's memory is refused, since the kernels run on `dev`
+// and would read it over a peer mapping that may not exist.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -111,7 +115,13 @@ extern "C" int beor_dbar_factored_noalloc(const beor_c128* A, const beor_c128* W
   if (!A || !W || !noise_var || !d || !dbar_out) return BEOR_EINVAL;
   if (nf <= 0 || ntb <= 0 || ncells <= 0 || nx <= 0) return BEOR_EINVAL;
   if ((int64_t)nf * ncells > kNoallocMaxU || nf > 65535) return BEOR_EINVAL;   // beyond the fixed scratch
-  if (!on_device(A) || !on_device(W) || !on_device(noise_var) || !on_device(d) || !on_device(dbar_out))
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return BEOR_ECUDA;
+  }
+  if (!on_device(A, dev) || !on_device(W, dev) || !on_device(noise_var, dev) || !on_device(d, dev) ||
+      !on_device(dbar_out, dev))
     return BEOR_EINVAL;
   double2* u = nullptr;
   int r = noalloc_scratch(&u);
