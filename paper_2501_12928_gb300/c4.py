@@ -43,7 +43,12 @@ def main(argv=None):
     lk.set_instrument(inst.A, inst.W, inst.kbin, inst.spec.n_k, inst.spec.lssm_prior_var)
     lk.set_data(inst.d, inst.noise_var)
     lk.precompute()
-    exact = ExactLikelihood(lk, max_batch=256)
+    # points the mixed path flags (status -1) are re-evaluated in float64
+    fb = Likelihood("fp64")
+    fb.set_instrument(inst.A, inst.W, inst.kbin, inst.spec.n_k, inst.spec.lssm_prior_var)
+    fb.set_data(inst.d, inst.noise_var)
+    fb.precompute()
+    exact = ExactLikelihood(lk, max_batch=256, fallback=fb)
     out = {"config": args.config, "n_model": inst.spec.n_model, "n_k": inst.spec.n_k, "args": vars(args)}
 
     t0 = time.perf_counter()
@@ -62,6 +67,7 @@ def main(argv=None):
         res = compare_runs(exact, model, inst.spec.n_k, delta_u=5.0 * model.rms_u, n_live=args.n_live,
                            k_remove=args.k_remove, batch=args.batch, seed=args.seed)
     out["runs"] = res
+    out["n_flagged_total"] = exact.n_flagged
     print(json.dumps(out, default=float))
 
 

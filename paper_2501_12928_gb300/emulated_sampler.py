@@ -20,30 +20,59 @@ from .beor import Emulator, Likelihood
 from .ns import NestedSampler
 
 
+def _pow2_pad(blk):
+    """blk padded to the next power of two by repeating its last row."""
+    b = 1
+    while b < len(blk):
+        b *= 2
+    return np.concatenate([blk, np.repeat(blk[-1:], b - len(blk), axis=0)]) if b > len(blk) else blk
+
+
 class ExactLikelihood:
     """Batched exact lnL(phi) through the C ABI.  Batches are padded to powers
     of two (one captured graph per size); padding rows are not counted.  With
-    `record` set, every evaluated (phi, lnL) pair is kept (training data)."""
+    `record` set, every evaluated (phi, lnL) pair is kept (training data).
 
-    def __init__(self, like: Likelihood, max_batch: int = 256):
+    Per-point status: a failed pivot (status > 0) or a non-finite phi
+    (status -2) gives lnL = -inf.  A mixed-precision result flagged as
+    possibly outside its tolerance (status -1) is not used as it stands:
+    it is re-evaluated on `fallback` (a float64 Likelihood of the same
+    instrument) when one is given, else rejected (-inf), so that no flagged
+    value becomes an accepted point, a training label or an evidence term.
+    `n_flagged` counts such points and `n_fallback` those re-evaluated."""
+
+    def __init__(self, like: Likelihood, max_batch: int = 256, fallback: Likelihood | None = None):
         self.like = like
+        self.fallback = fallback
         self.max_batch = max_batch
         self.n_calls = 0
         self.n_points = 0
+        self.n_flagged = 0
+        self.n_fallback = 0
         self.record = False
         self.rec_x, self.rec_l = [], []
+
+    def _fallback(self, phi):
+        out = np.full(len(phi), -np.inf)
+        for i in range(0, len(phi), self.max_batch):
+            blk = phi[i:i + self.max_batch]
+            l, st = self.fallback.lnl(_pow2_pad(blk))
+            out[i:i + len(blk)] = np.where(st[: len(blk)] != 0, -np.inf, l[: len(blk)])
+        self.n_fallback += len(phi)
+        return out
 
     def __call__(self, x):
         x = np.atleast_2d(np.asarray(x, np.float64))
         out = np.empty(len(x))
         for i in range(0, len(x), self.max_batch):
             blk = x[i:i + self.max_batch]
-            b = 1
-            while b < len(blk):
-                b *= 2
-            pad = np.concatenate([blk, np.repeat(blk[-1:], b - len(blk), axis=0)]) if b > len(blk) else blk
-            l, st = self.like.lnl(pad)
-            l = np.where(st[: len(blk)] > 0, -np.inf, l[: len(blk)])
+            l, st = self.like.lnl(_pow2_pad(blk))
+            st = np.asarray(st[: len(blk)])
+            l = np.where((st > 0) | (st == -2), -np.inf, l[: len(blk)])
+            flagged = np.flatnonzero(st == -1)
+            if len(flagged):
+                self.n_flagged += len(flagged)
+                l[flagged] = self._fallback(blk[flagged]) if self.fallback is not None else -np.inf
             out[i:i + len(blk)] = l
             self.n_calls += 1
             self.n_points += len(blk)
@@ -184,6 +213,7 @@ def compare_runs_active(exact: ExactLikelihood, phi0, lnl0, n_k: int, n_live=500
     out = {}
     for name in ("exact", "emulator"):
         exact.n_points = 0
+        flagged0, fallback0 = exact.n_flagged, exact.n_fallback
         exact.record = name == "emulator"
         t0 = time.perf_counter()
         scr = ActiveScreen(exact, phi0, lnl0, every=every, **train_kw) if name == "emulator" else None
@@ -194,7 +224,8 @@ def compare_runs_active(exact: ExactLikelihood, phi0, lnl0, n_k: int, n_live=500
         exact.record = False
         out[name] = {"logz": r.logz, "logz_err": r.logz_err, "h": r.h, "n_exact": r.n_exact,
                      "n_screened": r.n_screened, "n_iter": r.n_iter, "seconds": time.perf_counter() - t0,
-                     "refits": scr.refits if scr else 0}
+                     "refits": scr.refits if scr else 0, "n_flagged": exact.n_flagged - flagged0,
+                     "n_fallback": exact.n_fallback - fallback0}
     out["dlogz"] = out["emulator"]["logz"] - out["exact"]["logz"]
     out["same_sequence"] = out["emulator"]["n_iter"] == out["exact"]["n_iter"] and abs(out["dlogz"]) < 1e-9
     out["exact_eval_ratio"] = out["emulator"]["n_exact"] / max(1, out["exact"]["n_exact"])
@@ -208,12 +239,14 @@ def compare_runs(exact: ExactLikelihood, model: ScreenModel, n_k: int, delta_u: 
     out = {}
     for name, screen in (("exact", None), ("emulator", model.screen(delta_u))):
         exact.n_points = 0
+        flagged0, fallback0 = exact.n_flagged, exact.n_fallback
         t0 = time.perf_counter()
         ns = NestedSampler(exact, n_k, n_live=n_live, k_remove=k_remove, batch=batch, seed=seed,
                            screen=screen, screen_delta=0.0, screen_limit=model.support_limit)
         r = ns.run()
         out[name] = {"logz": r.logz, "logz_err": r.logz_err, "h": r.h, "n_exact": r.n_exact,
                      "n_screened": r.n_screened, "n_iter": r.n_iter, "seconds": time.perf_counter() - t0,
+                     "n_flagged": exact.n_flagged - flagged0, "n_fallback": exact.n_fallback - fallback0,
                      "posterior_mean": (r.posterior()[0] * r.posterior()[1][:, None]).sum(axis=0).tolist()}
     out["dlogz"] = out["emulator"]["logz"] - out["exact"]["logz"]
     # identical accepted sequences (no false negative of the screen) give identical runs
