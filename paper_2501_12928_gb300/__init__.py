@@ -17,4 +17,5 @@ from .beor import (  # noqa: F401
     KERNEL_CLASSES,
     set_lookahead,
     set_profiling,
+    set_wait_test,
 )

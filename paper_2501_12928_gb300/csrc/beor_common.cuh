@@ -17,7 +17,39 @@
 #define BEOR_TB 128                       // tile edge (complex rows / cols)
 #define BEOR_TILE_ELEMS (BEOR_TB * BEOR_TB)
 #define BEOR_NSLICE 5                     // bf16 slices per real value (mixed path)
-#define BEOR_NPLANE (2 * BEOR_NSLICE)     // (slice, re/im) planes
+#define BEOR_NPART 3                      // parts per slice: imaginary, real, negated imaginary
+#define BEOR_NPLANE (BEOR_NPART * BEOR_NSLICE)
+// Part order within a slice.  Windows of two consecutive parts are the
+// tensor cores' B operands of a complex product C += A B^H computed as real
+// products into [re | im] accumulator pairs: (im, re) multiplies Im A
+// (re += Ai Bi, im += Ai Br) and (re, -im) multiplies Re A (re += Ar Br,
+// im -= Ar Bi).
+#define BEOR_PART_IM 0
+#define BEOR_PART_RE 1
+#define BEOR_PART_NEGIM 2
+__host__ __device__ __forceinline__ int slice_plane(int slice, int part) { return slice * BEOR_NPART + part; }
+
+// Tensor-core products of one A slice sa (0..4) with a two-part B window in
+// the slice GEMM.  Slice pair (sa, t) belongs to level min(sa + t, 3), pairs
+// with sa + t > 4 are dropped; the accumulators are four levels of 128 TMEM
+// columns, each a [re | im] pair of 64.  The window's slices t = 0..3-sa feed
+// levels sa..3, contiguous in TMEM and in the window, so they take one
+// product per two levels (N = 256 or 128); the pair t = 4 - sa adds into
+// level 3.  Product q < slice_mma_count(sa) reads the window from slice
+// slice_mma_t(sa, q) on, writes N = slice_mma_n(sa, q) columns from TMEM
+// column slice_mma_col(sa, q).
+__host__ __device__ __forceinline__ int slice_mma_count(int sa) { return (5 - sa) / 2 + 1; }
+__host__ __device__ __forceinline__ int slice_mma_t(int sa, int q) {
+  return q + 1 < slice_mma_count(sa) ? 2 * q : 4 - sa;
+}
+__host__ __device__ __forceinline__ int slice_mma_col(int sa, int q) {
+  return q + 1 < slice_mma_count(sa) ? 128 * (sa + 2 * q) : 384;
+}
+__host__ __device__ __forceinline__ int slice_mma_n(int sa, int q) {
+  if (q + 1 == slice_mma_count(sa)) return 128;
+  const int left = 4 - sa - 2 * q;   // levels still to cover
+  return 128 * (left < 2 ? left : 2);
+}
 
 // Element (row, col) of one bf16 slice plane of `rows` rows x 128 columns
 // (col = the GEMM's K index).  The plane is stored in the order in which the

@@ -47,7 +47,7 @@ struct BatchView {
   double* resid;             // [P] accuracy indicator (see beor_stats.resid_rel_max)
   Flags* flags;
   // mixed path slice buffers
-  __nv_bfloat16* panel_sl;   // 2 buffers (block step parity) of NPLANE planes of rows x 128 (slice_elem_off order), plane = part * NSLICE + slice
+  __nv_bfloat16* panel_sl;   // 2 buffers (block step parity) of NPLANE planes of rows x 128 (slice_elem_off order), plane = slice_plane(slice, part)
   int32_t* panel_exp;        // 2 buffers of [rows]
   __nv_bfloat16* linv_sl;    // NPLANE planes of (P*128) x 128, slice_elem_off order
   int32_t* linv_exp;         // [P*128]

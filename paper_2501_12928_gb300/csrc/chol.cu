@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int kg, int mixe
   // balanced base-256 digits of round(x * 2^(39 - e)), x = hi + lo (scaled
   // exactly by a power of two, rounded once)
   const int64_t lrows = (int64_t)v.P * BEOR_TB;
-  const int64_t ps = lrows * BEOR_TB;   // planes [part][slice]: slice stride is one plane
+  const int64_t ps = lrows * BEOR_TB;   // one plane; plane index slice_plane(slice, part)
   for (int c = warp; c < BEOR_TB; c += nwarp) {
     float mx = 0.0f;
     for (int m = lane; m <= c; m += 32) {
@@ -433,9 +433,17 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int kg, int mixe
           X = (X - mm) >> 8;
         }
         dg[0] = (int)X;
-        __nv_bfloat16* dst = v.linv_sl + part * BEOR_NSLICE * ps + slice_elem_off(row, m, lrows);
+        __nv_bfloat16* dst = v.linv_sl + slice_elem_off(row, m, lrows);
 #pragma unroll
-        for (int sl = 0; sl < BEOR_NSLICE; ++sl) dst[sl * ps] = __float2bfloat16_rn(ldexpf((float)dg[sl], -8 * sl));
+        for (int sl = 0; sl < BEOR_NSLICE; ++sl) {
+          const float d = ldexpf((float)dg[sl], -8 * sl);
+          if (part == 0) {
+            dst[slice_plane(sl, BEOR_PART_RE) * ps] = __float2bfloat16_rn(d);
+          } else {
+            dst[slice_plane(sl, BEOR_PART_IM) * ps] = __float2bfloat16_rn(d);
+            dst[slice_plane(sl, BEOR_PART_NEGIM) * ps] = __float2bfloat16_rn(-d);
+          }
+        }
       }
     }
   }

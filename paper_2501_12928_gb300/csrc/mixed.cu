@@ -20,14 +20,24 @@
 // degeneracy makes it (a float32-accumulated product does not).
 //
 // Kernel structure (one CTA per SM, persistent over output tiles of 128 rows
-// x 64 complex columns): warp 0 issues TMA loads of the slice planes into a
-// 3-stage shared-memory ring (K chunks of 16, stored in global memory in the
-// tensor cores' no-swizzle order and fetched as 512-byte rows), warp 1 issues
-// the tcgen05.mma instructions (M = 128, N = 64..256, K = 16, bf16 -> fp32)
-// into eight TMEM accumulators (4 levels x re/im, all 512 columns), and
-// warps 2-9 (two per TMEM lane quarter, each with half the columns) drain
-// TMEM and apply the update.  Every wait is bounded by a %globaltimer deadline; on expiry
-// the kernel records an error code, drains what it issued and returns.
+// x 64 complex columns).  The accumulators of a tile are four levels, each a
+// [re | im] pair of 64 fp32 columns (level l at TMEM columns 128 l .. 128 l +
+// 127, all 512 columns).  The complex product C += A B^H is computed as real
+// products of one A part with a two-part window of B: Im A times the window
+// (Im B, Re B) adds (Ai Bi, Ai Br) to (re, im), and Re A times (Re B, -Im B)
+// adds (Ar Br, -Ar Bi), so one MMA covers the real and imaginary outputs of
+// up to two levels (N up to 256): 11 MMAs per A part and K-chunk instead of
+// 18 with separate re / im accumulators, which cuts the tensor cores' reads
+// of A from shared memory by 40 %.  The slice planes hold the parts
+// (Im, Re, -Im) of each slice for that reason.  Warp 0 issues TMA loads into
+// a 5-slot shared-memory ring of half-stages (one A part of 128 rows and its
+// B window of 64 rows, every slice, one K-chunk of 16: 40 KB), fetched from
+// the planes stored in the tensor cores' no-swizzle order as 512-byte rows;
+// warp 1 issues the tcgen05.mma instructions (M = 128, N = 128 or 256,
+// K = 16, bf16 -> fp32); warps 2-9 (two per TMEM lane quarter, each with half
+// the columns) drain TMEM and apply the update.  Every wait is bounded by a
+// %globaltimer deadline; on expiry the kernel records an error code, drains
+// what it issued and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -43,11 +53,13 @@ namespace beor {
 constexpr int MX_M = 128;                // output rows per tile
 constexpr int MX_N = 64;                 // output complex columns per tile
 constexpr int MX_KC = 16;                // complex K per pipeline stage
-constexpr int MX_STAGES = 3;
-constexpr int MX_A_BYTES = BEOR_NPLANE * MX_M * MX_KC * 2;   // 40960
-constexpr int MX_B_BYTES = BEOR_NPLANE * MX_N * MX_KC * 2;   // 20480
-constexpr int MX_STAGE_BYTES = MX_A_BYTES + MX_B_BYTES;      // 61440
-constexpr int MX_SMEM = MX_STAGES * MX_STAGE_BYTES + 1024 + 256;
+constexpr int MX_SLOTS = 5;              // half-stage ring (two half-stages per K-chunk)
+constexpr int MX_A_BYTES = BEOR_NSLICE * MX_M * MX_KC * 2;       // 20480: one A part, every slice
+constexpr int MX_B_BYTES = BEOR_NSLICE * 2 * MX_N * MX_KC * 2;   // 20480: a two-part B window, every slice
+constexpr int MX_HALF_BYTES = MX_A_BYTES + MX_B_BYTES;            // 40960
+constexpr int MX_SLICE_A = MX_M * MX_KC * 2;                      // 4096: one slice of the A part
+constexpr int MX_SLICE_B = 2 * MX_N * MX_KC * 2;                  // 4096: one slice of the B window
+constexpr int MX_SMEM = MX_SLOTS * MX_HALF_BYTES + 1024 + 256;   // 206080
 constexpr int MX_EPI_WARPS = 8;        // two warps per TMEM lane quarter, each draining half the columns
 constexpr int MX_THREADS = 64 + 32 * MX_EPI_WARPS;
 constexpr uint32_t MX_TMEM_COLS = 512;
@@ -60,9 +72,9 @@ constexpr int MX_JOBS = 4;               // depth of the producer -> MMA / epilo
 enum { ERR_TMA_WAIT = 11, ERR_MMA_WAIT = 12, ERR_ACC_WAIT = 13, ERR_EPI_WAIT = 14 };
 
 struct MixedMaps {
-  CUtensorMap panel_a[2];   // panel slices (two buffers by step parity), box: 128 rows x one K-chunk x 10 planes
-  CUtensorMap panel_b[2];   // the same, box 64 rows
-  CUtensorMap linv_b;       // inverse-diagonal slices, box 64 rows
+  CUtensorMap panel_a[2];   // panel slices (two buffers by step parity), box: 128 rows x one K-chunk x 1 part x 5 slices
+  CUtensorMap panel_b[2];   // the same, box 64 rows x 2 parts
+  CUtensorMap linv_b;       // inverse-diagonal slices, box 64 rows x 2 parts
   int64_t* d_prefix = nullptr;   // [4][max_nt][P+1] tile prefix sums (kinds col, rest, panel, all)
   int* d_counter = nullptr;      // [4][max_nt] dynamic tile counters, zeroed before every evaluation
   int max_nt = 0, P = 0;
@@ -122,11 +134,12 @@ __device__ __forceinline__ bool mbar_wait_deadline(uint32_t a, uint32_t parity) 
     if ((it & 255u) == 255u && globaltimer() - t0 > MX_TIMEOUT_NS) return false;
   }
 }
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
-                                            uint32_t mbar) {
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                            int u, uint32_t mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(mbar)
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(u), "r"(mbar)
       : "memory");
 }
 // Bulk prefetch of a contiguous global range into L2 (size a multiple of 16 bytes).
@@ -273,21 +286,23 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
                       int* __restrict__ counter, const int32_t* __restrict__ pexp) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + MX_STAGES * MX_STAGE_BYTES);
-  // bars[0..2] full, [3..5] empty, [6] acc_full, [7] acc_empty, [8] drain,
-  // [9..12] job_full, [13..16] job_empty
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 17);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 18);
-  TileJob* jobs = reinterpret_cast<TileJob*>(bars + 20);   // MX_JOBS slots
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + MX_SLOTS * MX_HALF_BYTES);
+  // bars[0..4] full, [5..9] empty, [10] acc_full, [11] acc_empty, [12] drain,
+  // [13..16] job_full, [17..20] job_empty; then the TMEM address, the abort
+  // flag and the job ring (256 bytes in all)
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 21);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 22);
+  TileJob* jobs = reinterpret_cast<TileJob*>(bars + 24);   // MX_JOBS slots
+  static_assert(24 * 8 + MX_JOBS * sizeof(TileJob) <= 256, "barrier area");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long wait_ns = v.wait_ns ? v.wait_ns : MX_TIMEOUT_NS;
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
-  auto empty_bar = [&](int s) { return bar0 + 8u * (3 + s); };
-  const uint32_t acc_full = bar0 + 8u * 6, acc_empty = bar0 + 8u * 7, drain = bar0 + 8u * 8;
-  auto job_full = [&](uint32_t q) { return bar0 + 8u * (9 + q); };
-  auto job_empty = [&](uint32_t q) { return bar0 + 8u * (13 + q); };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (MX_SLOTS + s); };
+  const uint32_t acc_full = bar0 + 8u * 10, acc_empty = bar0 + 8u * 11, drain = bar0 + 8u * 12;
+  auto job_full = [&](uint32_t q) { return bar0 + 8u * (13 + q); };
+  auto job_empty = [&](uint32_t q) { return bar0 + 8u * (17 + q); };
 
   // After a bounded wait gave up anywhere in this evaluation, the remaining
   // launches return at once (read by one thread, so the whole CTA agrees)
@@ -300,7 +315,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   }
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < MX_STAGES; ++s) {
+    for (int s = 0; s < MX_SLOTS; ++s) {
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
@@ -361,31 +376,35 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
                              tri_index(jb.i, jb.j) * BEOR_TILE_ELEMS + (int64_t)(jb.h * MX_N) * BEOR_TB;
           prefetch_l2(ct, (uint32_t)(MX_N * BEOR_TB * sizeof(float4)));
         }
-        for (int kc = 0; kc < BEOR_TB / MX_KC; ++kc, ++it) {
-          const int s = it % MX_STAGES;
-          const uint32_t ph = (it / MX_STAGES) & 1;
-          if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag, wait_ns)) {
-            atomicCAS(&v.flags->error, 0, ERR_TMA_WAIT);
-            *abort_flag = 1;
-            goto producer_done;
+        // two half-stages per K-chunk: h = 0 loads A part Im with the B window
+        // (Im, Re), h = 1 A part Re with the window (Re, -Im)
+        for (int kc = 0; kc < BEOR_TB / MX_KC; ++kc) {
+          for (int h = 0; h < 2; ++h, ++it) {
+            const int s = it % MX_SLOTS;
+            const uint32_t ph = (it / MX_SLOTS) & 1;
+            if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag, wait_ns)) {
+              atomicCAS(&v.flags->error, 0, ERR_TMA_WAIT);
+              *abort_flag = 1;
+              goto producer_done;
+            }
+            if (MODE == MODE_TRAIL && v.test_skip_copy && blockIdx.x == 0 && n == 0 && kc == 3 && h == 0) {
+              // test switch: no copy and no arrival for this half-stage, so
+              // the MMA warp's wait on it can only end by its limit
+              withheld = it;
+              continue;
+            }
+            mbar_expect_tx(full_bar(s), MX_HALF_BYTES);
+            const uint32_t dst = sbase + s * MX_HALF_BYTES;
+            // x = 0 always (16-byte aligned); y counts pairs of 8-row groups
+            tma_load_5d(dst, &map_a, 0, a_row / 16, kc, h, 0, full_bar(s));
+            tma_load_5d(dst + MX_A_BYTES, &map_b, 0, b_row / 16, kc, h, 0, full_bar(s));
           }
-          if (MODE == MODE_TRAIL && v.test_skip_copy && blockIdx.x == 0 && n == 0 && kc == 3) {
-            // test switch: no copy and no arrival for this stage, so the MMA
-            // warp's wait on it can only end by its limit
-            withheld = it;
-            continue;
-          }
-          mbar_expect_tx(full_bar(s), MX_STAGE_BYTES);
-          const uint32_t dst = sbase + s * MX_STAGE_BYTES;
-          // x = 0 always (16-byte aligned); y counts pairs of 8-row groups
-          tma_load_4d(dst, &map_a, 0, a_row / 16, kc, 0, full_bar(s));
-          tma_load_4d(dst + MX_A_BYTES, &map_b, 0, b_row / 16, kc, 0, full_bar(s));
         }
       }
     producer_done:
       // drain: every issued copy must have landed before the CTA may exit
-      for (uint32_t q = (it >= MX_STAGES ? it - MX_STAGES : 0); q < it; ++q)
-        if (q != withheld) mbar_wait_deadline(full_bar(q % MX_STAGES), (q / MX_STAGES) & 1);
+      for (uint32_t q = (it >= MX_SLOTS ? it - MX_SLOTS : 0); q < it; ++q)
+        if (q != withheld) mbar_wait_deadline(full_bar(q % MX_SLOTS), (q / MX_SLOTS) & 1);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -408,49 +427,36 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         }
         tc_fence_after();
         bool bad = false;
-        for (int kc = 0; kc < BEOR_TB / MX_KC; ++kc, ++it) {
-          const int s = it % MX_STAGES;
-          const uint32_t ph = (it / MX_STAGES) & 1;
-          if (!mbar_wait(full_bar(s), ph, abort_flag, wait_ns)) {
-            atomicCAS(&v.flags->error, 0, ERR_MMA_WAIT);
-            *abort_flag = 1;
-            bad = true;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t a0 = sbase + s * MX_STAGE_BYTES, b0 = a0 + MX_A_BYTES;
-          // Planes are stored [part][slice] (part 0 re, 1 im), so the B slices
-          // t = 0..3-sa are contiguous rows: one MMA with N = 64 (4 - sa)
-          // writes the level accumulators sa..3 at once (TMEM columns: re
-          // levels 0..3 in [0, 256), im levels in [256, 512)); the pair
-          // t = 4 - sa adds into level 3 with N = 64.
+        for (int kc = 0; kc < BEOR_TB / MX_KC && !bad; ++kc) {
+          for (int h = 0; h < 2; ++h, ++it) {
+            const int s = it % MX_SLOTS;
+            const uint32_t ph = (it / MX_SLOTS) & 1;
+            if (!mbar_wait(full_bar(s), ph, abort_flag, wait_ns)) {
+              atomicCAS(&v.flags->error, 0, ERR_MMA_WAIT);
+              *abort_flag = 1;
+              bad = true;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = sbase + s * MX_HALF_BYTES, b0 = a0 + MX_A_BYTES;
+            // A slice sa times B slices t contributes to level min(sa + t, 3)
+            // (schedule: slice_mma_*); the window's slices lie at 4 KB steps in
+            // shared memory, their two parts 64 rows apart, so that a product
+            // over two levels reads 256 consecutive rows.  The first two
+            // products of a tile (K-chunk 0, part Im, slice 0) cover all 512
+            // columns and overwrite them.
 #pragma unroll
-          for (int sa = 0; sa < BEOR_NSLICE; ++sa) {
-            const uint64_t ar = sdesc_kmajor(a0 + (0 * BEOR_NSLICE + sa) * (MX_M * 32));
-            const uint64_t ai = sdesc_kmajor(a0 + (1 * BEOR_NSLICE + sa) * (MX_M * 32));
-            const uint32_t acc0 = (kc == 0 && sa == 0) ? 0u : 1u;
-            if (sa <= 3) {
-              const uint32_t n = (uint32_t)MX_N * (4 - sa);
-              const uint64_t br = sdesc_kmajor(b0 + (0 * BEOR_NSLICE + 0) * (MX_N * 32));
-              const uint64_t bi = sdesc_kmajor(b0 + (1 * BEOR_NSLICE + 0) * (MX_N * 32));
-              const uint32_t d_re = tmem + (uint32_t)(sa * MX_N), d_im = tmem + 256u + (uint32_t)(sa * MX_N);
-              tc_mma(d_re, ar, br, idesc_bf16(0, n), acc0);
-              tc_mma(d_re, ai, bi, idesc_bf16(0, n), 1u);
-              tc_mma(d_im, ai, br, idesc_bf16(0, n), acc0);
-              tc_mma(d_im, ar, bi, idesc_bf16(1, n), 1u);
+            for (int sa = 0; sa < BEOR_NSLICE; ++sa) {
+              const uint64_t ad = sdesc_kmajor(a0 + sa * MX_SLICE_A);
+#pragma unroll
+              for (int q = 0; q < slice_mma_count(sa); ++q) {
+                const uint32_t acc = (kc == 0 && h == 0 && sa == 0 && q + 1 < slice_mma_count(sa)) ? 0u : 1u;
+                tc_mma(tmem + (uint32_t)slice_mma_col(sa, q), ad, sdesc_kmajor(b0 + slice_mma_t(sa, q) * MX_SLICE_B),
+                       idesc_bf16(0, (uint32_t)slice_mma_n(sa, q)), acc);
+              }
             }
-            {
-              const int tb = 4 - sa;
-              const uint64_t br = sdesc_kmajor(b0 + (0 * BEOR_NSLICE + tb) * (MX_N * 32));
-              const uint64_t bi = sdesc_kmajor(b0 + (1 * BEOR_NSLICE + tb) * (MX_N * 32));
-              const uint32_t d_re = tmem + 3u * MX_N, d_im = tmem + 256u + 3u * MX_N;
-              tc_mma(d_re, ar, br, idesc_bf16(0, MX_N), 1u);
-              tc_mma(d_re, ai, bi, idesc_bf16(0, MX_N), 1u);
-              tc_mma(d_im, ai, br, idesc_bf16(0, MX_N), 1u);
-              tc_mma(d_im, ar, bi, idesc_bf16(1, MX_N), 1u);
-            }
+            tc_commit(empty_bar(s));
           }
-          tc_commit(empty_bar(s));
         }
         if (bad) break;
         tc_commit(acc_full);
@@ -508,8 +514,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         float lr[4][4], li[4][4];
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
-          tmem_ld4(trow + (uint32_t)(l * MX_N + cbeg + c0), lr[l]);
-          tmem_ld4(trow + 256u + (uint32_t)(l * MX_N + cbeg + c0), li[l]);
+          tmem_ld4(trow + (uint32_t)(l * 128 + cbeg + c0), lr[l]);
+          tmem_ld4(trow + (uint32_t)(l * 128 + MX_N + cbeg + c0), li[l]);
         }
         tmem_ld_wait();
 #pragma unroll
@@ -630,7 +636,7 @@ __global__ void __launch_bounds__(256)
     for (int u = 0; u < 2; ++u) {
       const float4 a = s[c0 + q + u][r];
 #pragma unroll
-      for (int part = 0; part < 2; ++part) {
+      for (int part = 0; part < 2; ++part) {   // 0: real, 1: imaginary
         const float hi = part ? a.z : a.x, lo = part ? a.w : a.y;
         // balanced base-256 digits of the fixed-point number round(x * 2^(39 - e))
         long long X = 0;
@@ -644,7 +650,15 @@ __global__ void __launch_bounds__(256)
         }
         dg[0] = (int)X;
 #pragma unroll
-        for (int sl = 0; sl < BEOR_NSLICE; ++sl) val[u][part * BEOR_NSLICE + sl] = ldexpf((float)dg[sl], -8 * sl);
+        for (int sl = 0; sl < BEOR_NSLICE; ++sl) {
+          const float d = ldexpf((float)dg[sl], -8 * sl);
+          if (part == 0) {
+            val[u][slice_plane(sl, BEOR_PART_RE)] = d;
+          } else {
+            val[u][slice_plane(sl, BEOR_PART_IM)] = d;
+            val[u][slice_plane(sl, BEOR_PART_NEGIM)] = -d;
+          }
+        }
       }
     }
 #pragma unroll
@@ -688,19 +702,23 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// Slice planes in slice_elem_off order seen as a 4-D tensor: 256 elements
-// (two 8-row groups, 512 contiguous bytes) x rows/16 x 8 K-chunks x 10
-// planes.  A box of box_rows rows of one K-chunk of every plane is exactly
-// the shared-memory operand image (no swizzle), fetched as 512-byte rows.
-static cudaError_t make_map(CUtensorMap* m, void* base, int64_t rows, int box_rows) {
+// Slice planes in slice_elem_off order seen as a 5-D tensor: 256 elements
+// (two 8-row groups, 512 contiguous bytes) x rows/16 x 8 K-chunks x 3 parts
+// x 5 slices (plane = slice * 3 + part).  A box of box_rows rows of one
+// K-chunk, `parts` consecutive parts from a given one and every slice is
+// exactly the shared-memory operand image (no swizzle), fetched as 512-byte
+// rows: [slice][part][rows] of 8-row x 16-byte core matrices.
+static cudaError_t make_map(CUtensorMap* m, void* base, int64_t rows, int box_rows, int parts) {
   auto enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
   if (rows % 16 || box_rows % 16) return cudaErrorInvalidValue;
-  cuuint64_t dims[4] = {256, (cuuint64_t)(rows / 16), (cuuint64_t)(BEOR_TB / MX_KC), (cuuint64_t)BEOR_NPLANE};
-  cuuint64_t strides[3] = {512, (cuuint64_t)rows * MX_KC * 2, (cuuint64_t)rows * BEOR_TB * 2};
-  cuuint32_t box[4] = {256, (cuuint32_t)(box_rows / 16), 1, (cuuint32_t)BEOR_NPLANE};
-  cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es,
+  cuuint64_t dims[5] = {256, (cuuint64_t)(rows / 16), (cuuint64_t)(BEOR_TB / MX_KC), (cuuint64_t)BEOR_NPART,
+                        (cuuint64_t)BEOR_NSLICE};
+  cuuint64_t strides[4] = {512, (cuuint64_t)rows * MX_KC * 2, (cuuint64_t)rows * BEOR_TB * 2,
+                           (cuuint64_t)rows * BEOR_TB * 2 * BEOR_NPART};
+  cuuint32_t box[5] = {256, (cuuint32_t)(box_rows / 16), 1, (cuuint32_t)parts, (cuuint32_t)BEOR_NSLICE};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -711,10 +729,10 @@ cudaError_t mixed_maps_create(const BatchView& v, MixedMaps** out) {
   MixedMaps* m = new MixedMaps();
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-    e = make_map(&m->panel_a[b], slice_buf(v, b), v.rows, MX_M);
-    if (e == cudaSuccess) e = make_map(&m->panel_b[b], slice_buf(v, b), v.rows, MX_N);
+    e = make_map(&m->panel_a[b], slice_buf(v, b), v.rows, MX_M, 1);
+    if (e == cudaSuccess) e = make_map(&m->panel_b[b], slice_buf(v, b), v.rows, MX_N, 2);
   }
-  if (e == cudaSuccess) e = make_map(&m->linv_b, v.linv_sl, (int64_t)v.P * BEOR_TB, MX_N);
+  if (e == cudaSuccess) e = make_map(&m->linv_b, v.linv_sl, (int64_t)v.P * BEOR_TB, MX_N, 2);
   if (e != cudaSuccess) {
     delete m;
     return e;

@@ -1,19 +1,30 @@
 """The bf16 slice planes' storage order against the tensor maps and the
-tensor-core descriptors that read it, checked on the host.
+tensor-core descriptors that read it, and the slice GEMM's product schedule,
+checked on the host.
 
 A small host program is compiled against the library's own
 `beor_common.cuh` (nvcc, no GPU needed) and checks, for planes of 128, 256
 and 384 rows:
 
 * `slice_elem_off` is a bijection of (row, col) onto the plane;
-* reading a 4-D TMA box of the slice tensor map (256 contiguous elements x
-  box_rows / 16 x one K-chunk, box order with x fastest) for every 128-row
-  (A operand) and 64-row (B operand) block and every K-chunk places element
-  (r, c) of the block at byte (r / 8) * 256 + ((c % 16) / 8) * 128 +
-  (r % 8) * 16 + (c % 8) * 2 of the shared-memory image: the K-major layout
-  without swizzle of 8-row x 16-byte core matrices, K halves 128 bytes apart
-  (the descriptors' leading byte offset) and 8-row groups 256 bytes apart
-  (their stride byte offset).
+* reading a 5-D TMA box of the slice tensor map (256 contiguous elements x
+  box_rows / 16 x one K-chunk x parts x 5 slices, box order with x fastest)
+  places element (r, c) of part p of slice s where the tensor-core
+  descriptors read it: for the A operand (one part, 128 rows) at
+  s * 4096 + core(r, c), for the B window (two parts, 64 rows) at row
+  n = (s - t0) * 128 + (p - p0) * 64 + r of a descriptor starting at window
+  slice t0, i.e. t0 * 4096 + core(n, c), where core(r, c) =
+  (r / 8) * 256 + ((c % 16) / 8) * 128 + (r % 8) * 16 + (c % 8) * 2 is the
+  K-major layout without swizzle of 8-row x 16-byte core matrices (K halves
+  128 bytes apart, 8-row groups 256 bytes apart).
+
+A second program emulates the schedule of tensor-core products
+(`slice_mma_*`, two half-stages per K-chunk: part Im of A with the window
+(Im, Re), part Re with (Re, -Im)) on integer digits and checks that every
+level's [re | im] accumulator pair equals the complex product
+sum over s + t in the level of A_s B_t^H (pairs with s + t > 4 dropped,
+s + t >= 3 in level 3), with the first products of a tile overwriting and
+every later one accumulating.
 """
 
 import os
@@ -30,6 +41,8 @@ PROGRAM = r"""
 #include <vector>
 #include "beor_common.cuh"
 
+static long long core(long long r, long long c) { return (r / 8) * 256 + ((c % 16) / 8) * 128 + (r % 8) * 16 + (c % 8) * 2; }
+
 int main() {
   long long bad = 0;
   for (long long rows : {128LL, 256LL, 384LL}) {
@@ -41,37 +54,139 @@ int main() {
         ++seen[(size_t)o];
       }
     for (int s : seen) bad += s != 1;
-    for (int box_rows : {128, 64})
-      for (long long r0 = 0; r0 + box_rows <= rows; r0 += box_rows)
-        for (int kc = 0; kc < 8; ++kc)
-          for (long long r = r0; r < r0 + box_rows; ++r)
-            for (int c = kc * 16; c < kc * 16 + 16; ++c) {
-              // tensor map: element (x, y, z, w) at x + 256 y + rows*16 z + rows*128 w
-              const long long within = slice_elem_off(r, c, rows) - (long long)kc * rows * 16;
-              if (within < 0 || within >= rows * 16) { ++bad; continue; }
-              const long long y = within / 256 - r0 / 16, x = within % 256;
-              if (y < 0 || y >= box_rows / 16) { ++bad; continue; }
-              const long long got = 2 * (y * 256 + x);
-              const long long rr = r - r0, cc = c - kc * 16;
-              const long long want = (rr / 8) * 256 + (cc / 8) * 128 + (rr % 8) * 16 + (cc % 8) * 2;
-              bad += got != want;
-            }
+    // A operand: 128 rows, one part p; B window: 64 rows, parts p0, p0 + 1
+    for (int box_rows : {128, 64}) {
+      const int nparts = box_rows == 128 ? 1 : 2;
+      for (int p0 = 0; p0 + nparts <= BEOR_NPART; ++p0)
+        for (long long r0 = 0; r0 + box_rows <= rows; r0 += box_rows)
+          for (int kc = 0; kc < 8; ++kc)
+            for (int sl = 0; sl < BEOR_NSLICE; ++sl)
+              for (int pt = p0; pt < p0 + nparts; ++pt)
+                for (long long r = r0; r < r0 + box_rows; ++r)
+                  for (int c = kc * 16; c < kc * 16 + 16; ++c) {
+                    // the element's place in the plane buffer, decomposed by the
+                    // tensor map's strides (elements): x + 256 y + rows*16 z +
+                    // rows*128 part + rows*128*3 slice
+                    const long long g = (long long)slice_plane(sl, pt) * rows * 128 + slice_elem_off(r, c, rows);
+                    const long long gs = g / (rows * 128 * BEOR_NPART), g1 = g % (rows * 128 * BEOR_NPART);
+                    const long long gp = g1 / (rows * 128), g2 = g1 % (rows * 128);
+                    const long long gz = g2 / (rows * 16), g3 = g2 % (rows * 16);
+                    if (gs != sl || gp != pt || gz != kc) { ++bad; continue; }
+                    const long long y = g3 / 256 - r0 / 16, x = g3 % 256;
+                    if (y < 0 || y >= box_rows / 16) { ++bad; continue; }
+                    // box order: x fastest, then y, the K-chunk (1), the part, the slice
+                    const long long got = 2 * ((((long long)sl * nparts + (pt - p0)) * (box_rows / 16) + y) * 256 + x);
+                    const long long rr = r - r0, cc = c - kc * 16;
+                    if (nparts == 1) {
+                      bad += got != sl * 4096 + core(rr, cc);
+                    } else {
+                      for (int t0 = 0; t0 <= sl; t0 += 2) {
+                        const long long n = (long long)(sl - t0) * 128 + (pt - p0) * 64 + rr;
+                        bad += got != (long long)t0 * 4096 + core(n, cc);
+                      }
+                    }
+                  }
+    }
   }
   std::printf("mismatches %lld\n", bad);
   return bad != 0;
 }
 """
 
+SCHEDULE = r"""
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+#include "beor_common.cuh"
 
-def test_slice_planes_match_tma_boxes_and_core_matrices(tmp_path):
+// Integer digits: A (m rows), B (64 rows), K = 3, real and imaginary parts
+// of 5 slices.  TMEM emulation: m lanes x 512 columns.
+int main() {
+  const int m = 4, nb = 64, K = 3;
+  long long A[2][BEOR_NSLICE][4][3], Bd[2][BEOR_NSLICE][64][3];   // [0] real, [1] imaginary
+  srand(7);
+  for (int p = 0; p < 2; ++p)
+    for (int s = 0; s < BEOR_NSLICE; ++s) {
+      for (int r = 0; r < m; ++r) for (int k = 0; k < K; ++k) A[p][s][r][k] = rand() % 257 - 128;
+      for (int r = 0; r < nb; ++r) for (int k = 0; k < K; ++k) Bd[p][s][r][k] = rand() % 257 - 128;
+    }
+  // B planes in the library's part order
+  auto bplane = [&](int s, int part, int r, int k) -> long long {
+    if (part == BEOR_PART_RE) return Bd[0][s][r][k];
+    if (part == BEOR_PART_IM) return Bd[1][s][r][k];
+    if (part == BEOR_PART_NEGIM) return -Bd[1][s][r][k];
+    return 1LL << 40;
+  };
+  std::vector<long long> T((size_t)m * 512, 777);   // stale contents must be overwritten
+  std::vector<int> written(512, 0);
+  long long bad = 0;
+  for (int kc = 0; kc < 2; ++kc)
+    for (int h = 0; h < 2; ++h) {
+      const int apart = h == 0 ? 1 : 0;            // half-stage 0: A part Im, 1: A part Re
+      const int p0 = h == 0 ? BEOR_PART_IM : BEOR_PART_RE;
+      for (int sa = 0; sa < BEOR_NSLICE; ++sa)
+        for (int q = 0; q < slice_mma_count(sa); ++q) {
+          const bool acc = !(kc == 0 && h == 0 && sa == 0 && q + 1 < slice_mma_count(sa));
+          const int col = slice_mma_col(sa, q), t0 = slice_mma_t(sa, q), n = slice_mma_n(sa, q);
+          if (col + n > 512 || n % 128 || n > 256 || n < 128) ++bad;
+          for (int j = 0; j < n; ++j) {
+            const int t = t0 + j / 128, part = p0 + (j / 64) % 2, br = j % 64;
+            if (t >= BEOR_NSLICE) { ++bad; continue; }
+            if (!acc) written[col + j] = 1;
+            else if (!written[col + j]) ++bad;           // accumulating into a column never overwritten
+            for (int r = 0; r < m; ++r) {
+              long long v = 0;
+              for (int k = 0; k < K; ++k) v += A[apart][sa][r][k] * bplane(t, part, br, k);
+              long long& d = T[(size_t)r * 512 + col + j];
+              d = acc ? d + v : v;
+            }
+          }
+        }
+    }
+  // expected: level l, re = sum Ar Br + Ai Bi, im = sum Ai Br - Ar Bi over pairs in the level
+  // (twice: two K-chunks of the same data)
+  for (int l = 0; l < 4; ++l)
+    for (int r = 0; r < m; ++r)
+      for (int c = 0; c < nb; ++c) {
+        long long re = 0, im = 0;
+        for (int s = 0; s < BEOR_NSLICE; ++s)
+          for (int t = 0; t < BEOR_NSLICE; ++t) {
+            if (s + t > 4 || (s + t < 3 ? s + t : 3) != l) continue;
+            for (int k = 0; k < K; ++k) {
+              re += A[0][s][r][k] * Bd[0][t][c][k] + A[1][s][r][k] * Bd[1][t][c][k];
+              im += A[1][s][r][k] * Bd[0][t][c][k] - A[0][s][r][k] * Bd[1][t][c][k];
+            }
+          }
+        bad += T[(size_t)r * 512 + 128 * l + c] != 2 * re;
+        bad += T[(size_t)r * 512 + 128 * l + 64 + c] != 2 * im;
+      }
+  int nmma = 0;
+  for (int sa = 0; sa < BEOR_NSLICE; ++sa) nmma += slice_mma_count(sa);
+  std::printf("mismatches %lld products per half-stage %d\n", bad, nmma);
+  return bad != 0;
+}
+"""
+
+
+def _build_run(tmp_path, name, text):
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
-    src = tmp_path / "layout.cu"
-    exe = tmp_path / "layout"
-    src.write_text(PROGRAM)
+    src = tmp_path / f"{name}.cu"
+    exe = tmp_path / name
+    src.write_text(text)
     subprocess.run([nvcc, "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True,
                    capture_output=True, timeout=300)
-    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    return subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+
+
+def test_slice_planes_match_tma_boxes_and_core_matrices(tmp_path):
+    r = _build_run(tmp_path, "layout", PROGRAM)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "mismatches 0" in r.stdout
+
+
+def test_product_schedule_gives_each_level_its_complex_product(tmp_path):
+    r = _build_run(tmp_path, "schedule", SCHEDULE)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "mismatches 0 products per half-stage 11" in r.stdout
