@@ -220,6 +220,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true", help="skip the two-batches-in-flight measurement")
+    ap.add_argument("--no-tune", action="store_true", help="default schedule instead of the autotuner's")
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS),
                     help="c3: the sub-band mix (default); c1: the 3280-mode instrument (small profiling case)")
     args = ap.parse_args()
@@ -242,6 +243,13 @@ def main():
     likes = make_likes(P, insts, "mixed", names)
     torch.cuda.synchronize()
     t_pre = time.perf_counter() - t0
+    # schedule of this batch shape: the autotuner's choice (cached per box in the build folder)
+    tune = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        tune = P.autotune(likes, [phis[n] for n in names], reps=2,
+                          cache_path=os.path.join(ROOT, "paper_2501_12928_gb300", "_build", "schedule_cache.jsonl"))
+        tune["seconds"] = round(time.perf_counter() - t0, 1)
     stream = torch.cuda.current_stream()
     dev_phi = [torch.tensor(phis[n], dtype=torch.float64, device="cuda") for n in names]
     out = [torch.empty(args.B, dtype=torch.float64, device="cuda") for _ in names]
@@ -257,6 +265,7 @@ def main():
     if dist:
         dist.barrier()
     trail_ms, trail_n, cls_ms = 0.0, 0, {}
+    gap_any, gap_main, ms_eval = 0.0, 0.0, 0.0
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -269,6 +278,10 @@ def main():
             trail_n += st["n_class"]["trail"]
             for k, v in st["ms_class"].items():
                 cls_ms[k] = cls_ms.get(k, 0.0) + v
+            if st["ms_busy_any"] >= 0:
+                ms_eval += st["ms_last"]
+                gap_any += st["ms_last"] - st["ms_busy_any"]
+                gap_main += st["ms_last"] - st["ms_busy_main"]
         e1.record(stream)
         torch.cuda.synchronize()
     elapsed = e0.elapsed_time(e1) / 1e3
@@ -416,7 +429,14 @@ def main():
             "fp64_gpu": fp64,
             "two_in_flight": two,
             "speedup_vs_fp64_gpu": mix_value / fp64["value"] if fp64 else None,
+            "schedule": tune,
             "kernel_ms_per_step": {k: v / args.steps for k, v in cls_ms.items()},
+            "graph_gaps": {"ms_per_step": ms_eval / args.steps,
+                           "ms_no_kernel_in_flight": gap_any / args.steps,
+                           "ms_main_stream_idle": gap_main / args.steps,
+                           "how": "union of every launch's interval between the CUDA events that bracket it "
+                                  "inside the graph; the rest of the evaluation has no kernel launched and "
+                                  "unfinished on any stream (main stream alone: second figure)"},
             "status_all_ok": status_ok,
             "clocks": clk.summary(),
         }

@@ -189,6 +189,12 @@ typedef struct {
   int32_t device_error;     /* after BEOR_ETIMEOUT: the bounded wait that gave up first (11 copy
                                producer, 12 tensor-core issuer waiting for operands, 13 issuer
                                waiting for the accumulators, 14 epilogue); 0 otherwise */
+  double ms_busy_any;       /* profiling on: time of the last evaluation during which a kernel of
+                               any stream was launched and not finished (the union of the
+                               launches' intervals between their bracketing events); ms_last minus
+                               this is the time lost to the graph's dependencies and launch
+                               latencies.  -1 when not measured */
+  double ms_busy_main;      /* the same for the launches of the main stream alone */
 } beor_stats;
 int beor_get_stats(const beor_ctx *ctx, beor_stats *out);
 
@@ -208,6 +214,60 @@ int beor_set_profiling(int on);
  * Off: one stream, steps in order.
  * Float64 contexts always use the in-order schedule. */
 int beor_set_lookahead(int on);
+
+/* Schedule of the batched mixed-precision factorisation (the blocked
+ * right-looking Cholesky of every problem of a batch, run as a sequence of
+ * batched launches per block step, captured in one CUDA graph).  None of
+ * these settings changes an operation on any tile: factors and
+ * log-determinants are identical under every schedule (the float64
+ * residual of the quadratic form sums with atomics, so lnL may differ in
+ * its last bits).
+ *   lookahead:  1 = block step k's trailing update is split into the next
+ *               block column (high priority, main stream) and the rest
+ *               (low priority, second stream), so that the diagonal block,
+ *               slicing and panel of step k + 1 overlap the rest of step k;
+ *               0 = one stream, steps in order.
+ *   rest_ctas:  CTAs of each launch that updates block columns j >= k + 2
+ *               (persistent, tiles from a counter); 0 = one per SM.  Fewer
+ *               leave SMs to the main stream's kernels.
+ *   col_ctas:   the same for the next-column update and the panel product.
+ *   align_ends: 1 = in a batch of uneven sizes, smaller problems start late
+ *               so that all end on the last block step (their light final
+ *               steps overlap); 0 = all start on step 0. */
+typedef struct {
+  int lookahead;
+  int rest_ctas;
+  int col_ctas;
+  int align_ends;
+} beor_schedule;
+
+/* Set (sch != NULL) or reset to the default (NULL) the schedule of lnL
+ * evaluations of one batch shape: the model dimensions of ctxs (in order),
+ * their B and their precision.  Batches of that shape built under another
+ * schedule are released and rebuilt on their next use.  Default: lookahead
+ * as beor_set_lookahead, rest_ctas = col_ctas = 0, align_ends = 1.
+ * BEOR_EINVAL for B out of 1..4096 or negative CTA counts; BEOR_ESTATE for
+ * a context without a model. */
+int beor_set_schedule(beor_ctx *const *ctxs, int n_sets, const int *B, const beor_schedule *sch);
+int beor_get_schedule(beor_ctx *const *ctxs, int n_sets, const int *B, beor_schedule *out);
+
+/* Autotuner of the schedule for one batch shape (precomputed contexts,
+ * phi[s]: B[s] x n_k points in host or device memory, as for
+ * beor_lnl_multi).  If cache_path names a file holding an entry for this
+ * device and shape, that schedule is applied and returned without timing.
+ * Otherwise every candidate -- look-ahead on with rest_ctas in {one per SM,
+ * 8, 16, 24 fewer} and align_ends in {1, 0}, and look-ahead off with
+ * align_ends in {1, 0} -- is applied and timed: one untimed evaluation
+ * (building the batch and its graph), then `reps` evaluations (1..100),
+ * the fastest device time counting.  The fastest candidate is applied
+ * (beor_set_schedule) and, with cache_path, appended to the cache (one JSON
+ * object per line).  chosen, ms_chosen (its time per evaluation) and
+ * ms_default (the default schedule's time, -1 when read from the cache
+ * without it) may be NULL.  Float64 contexts have only the in-order
+ * schedule; the call then times it alone.  Allocates each candidate's
+ * workspaces in turn; BEOR_ENOMEM if one does not fit. */
+int beor_autotune(beor_ctx *const *ctxs, int n_sets, const double *const *phi, const int *B, int reps,
+                  const char *cache_path, beor_schedule *chosen, double *ms_chosen, double *ms_default);
 
 /* Test hook of the failure detection of the tensor-core kernels (process
  * wide, off by default: beor_set_wait_test(0, 0)).  Each role of those

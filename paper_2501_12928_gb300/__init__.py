@@ -18,4 +18,7 @@ from .beor import (  # noqa: F401
     set_lookahead,
     set_profiling,
     set_wait_test,
+    set_schedule,
+    get_schedule,
+    autotune,
 )

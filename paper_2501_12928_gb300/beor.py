@@ -54,6 +54,9 @@ def _load():
         "beor_set_profiling": [_c.c_int],
         "beor_set_lookahead": [_c.c_int],
         "beor_set_wait_test": [_c.c_int, _c.c_double],
+        "beor_set_schedule": [_P, _c.c_int, _P, _P],
+        "beor_get_schedule": [_P, _c.c_int, _P, _P],
+        "beor_autotune": [_P, _c.c_int, _P, _P, _c.c_int, _c.c_char_p, _P, _P, _P],
         "beor_dbar_factored_noalloc": [_P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _P, _P, _P, _P],
         "beor_mlp_create": [_c.POINTER(_P), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64],
         "beor_mlp_destroy": [_P],
@@ -93,7 +96,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [("refine_iters_max", ctypes.c_int), ("resid_rel_max", ctypes.c_double),
                 ("ms_last", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("ms_class", ctypes.c_double * 8), ("n_class", ctypes.c_int64 * 8),
-                ("device_error", ctypes.c_int32)]
+                ("device_error", ctypes.c_int32), ("ms_busy_any", ctypes.c_double),
+                ("ms_busy_main", ctypes.c_double)]
 
 
 KERNEL_CLASSES = ("init", "diag", "slice", "panel", "trail", "solve", "refine", "lnl")
@@ -110,6 +114,55 @@ def set_lookahead(on: bool):
 def set_wait_test(skip_one_copy: bool, limit_ms: float = 0.0):
     """Failure-detection test hook (see beor_set_wait_test); (False, 0) is the default."""
     _check(_lib().beor_set_wait_test(1 if skip_one_copy else 0, float(limit_ms)), "beor_set_wait_test")
+
+
+class Schedule(ctypes.Structure):
+    """beor_schedule: look-ahead, CTAs of the rest / next-column launches
+    (0 = one per SM), aligned ends."""
+    _fields_ = [("lookahead", ctypes.c_int), ("rest_ctas", ctypes.c_int), ("col_ctas", ctypes.c_int),
+                ("align_ends", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _shape(likes, Bs):
+    n = len(likes)
+    ctxs = (ctypes.c_void_p * n)(*[lk._h.value for lk in likes])
+    bb = (ctypes.c_int * n)(*[int(b) for b in Bs])
+    return n, ctxs, bb
+
+
+def set_schedule(likes: list, Bs: list, schedule: dict | None):
+    """Schedule of lnL evaluations of this batch shape (None: the default)."""
+    n, ctxs, bb = _shape(likes, Bs)
+    sch = Schedule(**schedule) if schedule is not None else None
+    _check(_lib().beor_set_schedule(ctypes.cast(ctxs, ctypes.c_void_p), n, ctypes.cast(bb, ctypes.c_void_p),
+                                    ctypes.byref(sch) if sch is not None else None), "beor_set_schedule")
+
+
+def get_schedule(likes: list, Bs: list) -> dict:
+    n, ctxs, bb = _shape(likes, Bs)
+    sch = Schedule()
+    _check(_lib().beor_get_schedule(ctypes.cast(ctxs, ctypes.c_void_p), n, ctypes.cast(bb, ctypes.c_void_p),
+                                    ctypes.byref(sch)), "beor_get_schedule")
+    return sch.as_dict()
+
+
+def autotune(likes: list, phis: list, reps: int = 2, cache_path: str | None = None) -> dict:
+    """Time the schedule candidates of this batch shape (see beor_autotune);
+    returns the chosen schedule and the times per evaluation."""
+    keep = []
+    phi_arr = [np.atleast_2d(np.asarray(p, np.float64)) for p in phis]
+    n, ctxs, bb = _shape(likes, [p.shape[0] for p in phi_arr])
+    pp = (ctypes.c_void_p * n)(*[_ptr(p, np.float64, keep).value for p in phi_arr])
+    sch = Schedule()
+    ms, ms0 = ctypes.c_double(-1.0), ctypes.c_double(-1.0)
+    _check(_lib().beor_autotune(ctypes.cast(ctxs, ctypes.c_void_p), n, ctypes.cast(pp, ctypes.c_void_p),
+                                ctypes.cast(bb, ctypes.c_void_p), int(reps),
+                                cache_path.encode() if cache_path else None, ctypes.byref(sch), ctypes.byref(ms),
+                                ctypes.byref(ms0)), "beor_autotune")
+    return {"schedule": sch.as_dict(), "ms_per_eval": ms.value, "ms_default": ms0.value}
 
 
 def _stream(stream):
@@ -237,6 +290,8 @@ class Likelihood:
         out["ms_class"] = dict(zip(KERNEL_CLASSES, list(st.ms_class)))
         out["n_class"] = dict(zip(KERNEL_CLASSES, list(st.n_class)))
         out["device_error"] = st.device_error
+        out["ms_busy_any"] = st.ms_busy_any
+        out["ms_busy_main"] = st.ms_busy_main
         return out
 
     def factor(self, b: int = 0):

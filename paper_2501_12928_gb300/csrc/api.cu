@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <string>
 #include <mutex>
 #include <vector>
 
@@ -22,7 +23,7 @@ constexpr int kRefineIters = 2;   // refinement steps of the mixed solve (fixed:
 constexpr int kClasses = 8;       // kernel classes timed when profiling is on
 enum { KC_INIT = 0, KC_DIAG, KC_SLICE, KC_PANEL, KC_TRAIL, KC_SOLVE, KC_REFINE, KC_LNL };
 bool g_profiling = false;
-bool g_lookahead = true;
+bool g_lookahead = true;      // default schedule of shapes without one of their own
 // bounded-wait test switch (beor_set_wait_test): role-wait limit (0 = the
 // kernels' own 2 s) and whether one operand copy is withheld
 unsigned long long g_wait_ns = 0;
@@ -128,11 +129,13 @@ struct Plan {
   bool refine_x = false;            // mixed: refine the solution (posterior mean) rather than correct q
   int slot = 0;                     // independent copies of one batch shape (asynchronous calls)
   bool lookahead = true;            // schedule of the mixed factorisation captured in the graph
+  beor_schedule sch{};              // the shape's schedule when the plan was built
   unsigned long long wait_ns = 0;   // bounded-wait settings captured in the graph
   int skip_copy = 0;
   int prio_hi = 0;                  // greatest stream priority of the device
   std::vector<cudaEvent_t> pev;     // boundary events (profiling)
   std::vector<int> pcls;            // class of the launch after each boundary event
+  std::vector<int> pstr;            // its stream: 0 main, 1 side (rest of the trailing update), 2 forward steps
   cudaStream_t side = nullptr;      // second stream of the look-ahead schedule (rest of the trailing update)
   cudaStream_t side2 = nullptr;     // third stream: forward substitution of dbar, step by step
   cudaEvent_t ev_col = nullptr, ev_rest = nullptr, ev_diag = nullptr, ev_fwd = nullptr;
@@ -176,7 +179,10 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
   int64_t L = 0;
   size_t ev_i = 0;
   cudaError_t e;
-  if (mark) pl.pcls.clear();
+  if (mark) {
+    pl.pcls.clear();
+    pl.pstr.clear();
+  }
   auto tick = [&](cudaStream_t on) -> cudaError_t {
     if (!mark) return cudaSuccess;
     if (ev_i >= pl.pev.size()) {
@@ -189,7 +195,10 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
   };
 #define RUN_ON(cls, on, x)            \
   do {                                \
-    if (mark) pl.pcls.push_back(cls); \
+    if (mark) {                       \
+      pl.pcls.push_back(cls);         \
+      pl.pstr.push_back(on == s ? 0 : on == pl.side ? 1 : 2); \
+    }                                 \
     e = tick(on);                     \
     if (e != cudaSuccess) return e;   \
     e = (x);                          \
@@ -310,6 +319,35 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
   return cudaSuccess;
 }
 
+// Schedules per batch shape: precision, lnL or posterior mean, and the
+// (model dimension, B) of every set in order.
+std::map<std::string, beor_schedule> g_schedules;
+
+std::string shape_key(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x) {
+  std::string k = "p" + std::to_string(ctxs[0]->precision) + (need_x ? "x1:" : "x0:");
+  for (int s = 0; s < nsets; ++s) k += std::to_string(ctxs[s]->n) + "x" + std::to_string(Bs[s]) + ",";
+  return k;
+}
+
+beor_schedule default_schedule() {
+  beor_schedule d{};
+  d.lookahead = g_lookahead ? 1 : 0;
+  d.rest_ctas = 0;
+  d.col_ctas = 0;
+  d.align_ends = 1;
+  return d;
+}
+
+beor_schedule schedule_of(const std::string& key) {
+  auto it = g_schedules.find(key);
+  return it == g_schedules.end() ? default_schedule() : it->second;
+}
+
+bool same_schedule(const beor_schedule& a, const beor_schedule& b) {
+  return a.lookahead == b.lookahead && a.rest_ctas == b.rest_ctas && a.col_ctas == b.col_ctas &&
+         a.align_ends == b.align_ends;
+}
+
 int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, int slot, Plan** out) {
   Plan* pl = new Plan();
   pl->refine_x = need_x;
@@ -355,10 +393,11 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, int
   }
   pl->P = (int)pl->h_prob.size();
   pl->rows = rows;
+  pl->sch = schedule_of(shape_key(ctxs, nsets, Bs, need_x));
   // mixed batches of uneven sizes: each problem starts max_nt - nt block steps
   // late, so that all end on the last step and the light late steps of the
   // largest problems overlap the heavy early steps of the smaller ones
-  for (Prob& pr : pl->h_prob) pr.k_off = pl->mixed ? pl->max_nt - pr.nt : 0;
+  for (Prob& pr : pl->h_prob) pr.k_off = pl->mixed && pl->sch.align_ends ? pl->max_nt - pr.nt : 0;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) {
     if (x != cudaSuccess && e == cudaSuccess) e = x;
@@ -432,6 +471,8 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, int
   v.rwork = pl->rwork.as<RWork>();
   v.n_rwork = pl->n_rwork;
   v.rows = rows;
+  v.grid_rest = pl->sch.rest_ctas;
+  v.grid_col = pl->sch.col_ctas;
   if (pl->mixed) {
     chk(mixed_maps_create(v, &pl->maps));
     int lo = 0, hi = 0;
@@ -460,6 +501,29 @@ Plan* find_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, in
     if (same) return p;
   }
   return nullptr;
+}
+
+// Plans whose schedule is no longer their shape's (after beor_set_schedule or
+// beor_set_lookahead) are released; the next call rebuilds them.
+void drop_plans_with_stale_schedule() {
+  std::vector<Plan*> keep;
+  bool synced = false;
+  for (Plan* p : g_plans) {
+    const beor_schedule cur = schedule_of(shape_key(p->ctxs.data(), (int)p->ctxs.size(), p->Bs.data(), p->refine_x));
+    if (!same_schedule(cur, p->sch)) {
+      if (!synced) {   // no evaluation of the plan may still be running
+        cudaSetDevice(p->device);
+        cudaDeviceSynchronize();
+        synced = true;
+      }
+      for (beor_ctx* o : p->ctxs)
+        if (o->last_plan == p) o->last_plan = nullptr;
+      delete p;
+    } else {
+      keep.push_back(p);
+    }
+  }
+  g_plans.swap(keep);
 }
 
 void drop_plans_of(beor_ctx* c) {
@@ -516,6 +580,14 @@ int set_kbin(beor_ctx* c, const int32_t* kbin, int64_t n, int n_k, double lssm) 
 }
 
 }  // namespace
+
+namespace beor {
+// Shape key and precision of a batch, for the autotuner (autotune.cu).
+std::string shape_key_of(beor_ctx* const* ctxs, int nsets, const int* B) {
+  return shape_key(ctxs, nsets, B, false);
+}
+bool is_mixed(const beor_ctx* c) { return c && c->precision == BEOR_PREC_MIXED; }
+}  // namespace beor
 
 extern "C" {
 
@@ -720,7 +792,7 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
   if (!pl->exec) {
     // first use: run once directly (sets kernel attributes), then capture
     int64_t nl = 0;
-    pl->lookahead = g_lookahead;
+    pl->lookahead = pl->sch.lookahead != 0;
     pl->wait_ns = g_wait_ns;
     pl->skip_copy = g_skip_copy;
     pl->view.wait_ns = g_wait_ns;
@@ -775,18 +847,52 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
     cudaGetLastError();
     ms = -1.0f;
   }
-  // per-class device time (profiled graphs only)
+  // per-class device time (profiled graphs only), and the evaluation's
+  // timeline: each launch's interval between its bracketing events (which
+  // includes any wait for SMs behind other streams' kernels); the time in
+  // which no launch of any stream is in flight is the cost of the graph's
+  // dependency edges and launch latencies
   double cls_ms[kClasses] = {0};
   int64_t cls_n[kClasses] = {0};
+  double busy_any = -1.0, busy_main = -1.0;
   if (pl->prof && ms >= 0.0f) {
+    std::vector<std::pair<double, double>> iv_all, iv_main;
+    bool ok = true;
     for (size_t i = 0; i < pl->pcls.size() && 2 * i + 1 < pl->pev.size(); ++i) {
-      float t = 0.0f;
+      float t = 0.0f, a = 0.0f, b = 0.0f;
       if (cudaEventElapsedTime(&t, pl->pev[2 * i], pl->pev[2 * i + 1]) == cudaSuccess) {
         cls_ms[pl->pcls[i]] += t;
         cls_n[pl->pcls[i]] += 1;
       } else {
         cudaGetLastError();
       }
+      if (cudaEventElapsedTime(&a, pl->ev0, pl->pev[2 * i]) == cudaSuccess &&
+          cudaEventElapsedTime(&b, pl->ev0, pl->pev[2 * i + 1]) == cudaSuccess) {
+        iv_all.emplace_back(a, b);
+        if (i < pl->pstr.size() && pl->pstr[i] == 0) iv_main.emplace_back(a, b);
+      } else {
+        cudaGetLastError();
+        ok = false;
+      }
+    }
+    auto union_len = [](std::vector<std::pair<double, double>>& iv) {
+      std::sort(iv.begin(), iv.end());
+      double tot = 0.0, cs = -1e300, ce = -1e300;
+      for (const auto& x : iv) {
+        if (x.first > ce) {
+          if (ce > cs) tot += ce - cs;
+          cs = x.first;
+          ce = x.second;
+        } else if (x.second > ce) {
+          ce = x.second;
+        }
+      }
+      if (ce > cs) tot += ce - cs;
+      return tot;
+    };
+    if (ok) {
+      busy_any = union_len(iv_all);
+      busy_main = union_len(iv_main);
     }
   }
   // diagnostics
@@ -805,6 +911,8 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
       c->stats.ms_class[q] = cls_ms[q];
       c->stats.n_class[q] = cls_n[q];
     }
+    c->stats.ms_busy_any = busy_any;
+    c->stats.ms_busy_main = busy_main;
     c->last_plan = pl;
     c->last_first = pl->first[s];
   }
@@ -917,9 +1025,7 @@ int beor_get_dbar(beor_ctx* c, beor_c128* out) {
 // graphs captured with another setting are rebuilt on their next use
 static void drop_stale_graphs() {
   for (Plan* p : g_plans) {
-    if ((p->prof != g_profiling || p->lookahead != g_lookahead || p->wait_ns != g_wait_ns ||
-         p->skip_copy != g_skip_copy) &&
-        p->exec) {
+    if ((p->prof != g_profiling || p->wait_ns != g_wait_ns || p->skip_copy != g_skip_copy) && p->exec) {
       cudaGraphExecDestroy(p->exec);
       cudaGraphDestroy(p->graph);
       p->exec = nullptr;
@@ -938,7 +1044,44 @@ int beor_set_profiling(int on) {
 int beor_set_lookahead(int on) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_lookahead = on != 0;
-  drop_stale_graphs();
+  drop_plans_with_stale_schedule();
+  return BEOR_OK;
+}
+
+static int check_shape(beor_ctx* const* ctxs, int nsets, const int* B) {
+  if (!ctxs || nsets <= 0 || !B) return BEOR_EINVAL;
+  for (int s = 0; s < nsets; ++s) {
+    if (!ctxs[s] || B[s] <= 0 || B[s] > 4096) return BEOR_EINVAL;
+    if (ctxs[s]->n <= 0) return BEOR_ESTATE;
+  }
+  return BEOR_OK;
+}
+
+int beor_set_schedule(beor_ctx* const* ctxs, int nsets, const int* B, const beor_schedule* sch) {
+  int r = check_shape(ctxs, nsets, B);
+  if (r) return r;
+  if (sch && (sch->rest_ctas < 0 || sch->col_ctas < 0 || sch->rest_ctas > 65535 || sch->col_ctas > 65535))
+    return BEOR_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  const std::string key = shape_key(ctxs, nsets, B, false);
+  if (sch) {
+    beor_schedule c = *sch;
+    c.lookahead = c.lookahead != 0;
+    c.align_ends = c.align_ends != 0;
+    g_schedules[key] = c;
+  } else {
+    g_schedules.erase(key);
+  }
+  drop_plans_with_stale_schedule();
+  return BEOR_OK;
+}
+
+int beor_get_schedule(beor_ctx* const* ctxs, int nsets, const int* B, beor_schedule* out) {
+  int r = check_shape(ctxs, nsets, B);
+  if (r) return r;
+  if (!out) return BEOR_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  *out = schedule_of(shape_key(ctxs, nsets, B, false));
   return BEOR_OK;
 }
 

@@ -1,0 +1,194 @@
+// Autotuner of the batched factorisation's schedule (beor_autotune).
+//
+// The schedule of a batch shape (look-ahead, CTA counts of the persistent
+// trailing / panel launches, aligned ends; see beor_schedule) changes only
+// the order and placement of the work, never an operation on a tile, so the
+// tuner may pick any candidate on time alone.  Each candidate is applied
+// with beor_set_schedule, its batch built and its graph captured by one
+// untimed evaluation, and then timed over `reps` evaluations through the
+// public call (device time of the graph launch, beor_stats.ms_last).  The
+// result is kept in a cache file of one JSON object per line, keyed by the
+// device name and the batch shape.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/beor.h"
+
+namespace beor {
+std::string shape_key_of(beor_ctx* const* ctxs, int nsets, const int* B);   // api.cu
+bool is_mixed(const beor_ctx* c);                                           // api.cu
+}  // namespace beor
+
+namespace {
+
+std::string device_name() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  char name[256] = {0};
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) std::snprintf(name, sizeof(name), "%s", p.name);
+  else cudaGetLastError();
+  return name;
+}
+
+// Value of "key": in a line written by write_entry (a flat JSON object).
+bool json_field(const std::string& line, const char* key, std::string* out) {
+  const std::string pat = std::string("\"") + key + "\": ";
+  const size_t at = line.find(pat);
+  if (at == std::string::npos) return false;
+  size_t i = at + pat.size();
+  if (i < line.size() && line[i] == '"') {
+    const size_t end = line.find('"', i + 1);
+    if (end == std::string::npos) return false;
+    *out = line.substr(i + 1, end - i - 1);
+    return true;
+  }
+  size_t end = i;
+  while (end < line.size() && line[end] != ',' && line[end] != '}') ++end;
+  *out = line.substr(i, end - i);
+  return true;
+}
+
+bool read_entry(const char* path, const std::string& dev, const std::string& key, beor_schedule* sch, double* ms,
+                double* ms_default) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  bool found = false;
+  char buf[1024];
+  while (std::fgets(buf, sizeof(buf), f)) {
+    const std::string line(buf);
+    std::string d, k, v;
+    if (!json_field(line, "device", &d) || !json_field(line, "shape", &k) || d != dev || k != key) continue;
+    beor_schedule s{};
+    double m = -1.0, md = -1.0;
+    int* fields[4] = {&s.lookahead, &s.rest_ctas, &s.col_ctas, &s.align_ends};
+    const char* names[4] = {"lookahead", "rest_ctas", "col_ctas", "align_ends"};
+    bool ok = true;
+    for (int q = 0; q < 4 && ok; ++q) {
+      ok = json_field(line, names[q], &v);
+      if (ok) *fields[q] = std::atoi(v.c_str());
+    }
+    if (json_field(line, "ms", &v)) m = std::atof(v.c_str());
+    if (json_field(line, "ms_default", &v)) md = std::atof(v.c_str());
+    if (!ok || s.rest_ctas < 0 || s.col_ctas < 0) continue;
+    *sch = s;   // the last matching entry wins
+    *ms = m;
+    *ms_default = md;
+    found = true;
+  }
+  std::fclose(f);
+  return found;
+}
+
+void write_entry(const char* path, const std::string& dev, const std::string& key, const beor_schedule& s, double ms,
+                 double ms_default) {
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f,
+               "{\"device\": \"%s\", \"shape\": \"%s\", \"lookahead\": %d, \"rest_ctas\": %d, \"col_ctas\": %d, "
+               "\"align_ends\": %d, \"ms\": %.4f, \"ms_default\": %.4f}\n",
+               dev.c_str(), key.c_str(), s.lookahead, s.rest_ctas, s.col_ctas, s.align_ends, ms, ms_default);
+  std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" int beor_autotune(beor_ctx* const* ctxs, int nsets, const double* const* phi, const int* B, int reps,
+                             const char* cache_path, beor_schedule* chosen, double* ms_chosen,
+                             double* ms_default) {
+  if (!ctxs || nsets <= 0 || !phi || !B || reps < 1 || reps > 100) return BEOR_EINVAL;
+  for (int s = 0; s < nsets; ++s)
+    if (!ctxs[s] || !phi[s] || B[s] <= 0 || B[s] > 4096) return BEOR_EINVAL;
+  beor_schedule cur{};
+  int r = beor_get_schedule(ctxs, nsets, B, &cur);
+  if (r) return r;
+  const std::string key = beor::shape_key_of(ctxs, nsets, B);
+  const std::string dev = device_name();
+  if (cache_path) {
+    beor_schedule s{};
+    double m = -1.0, md = -1.0;
+    if (read_entry(cache_path, dev, key, &s, &m, &md)) {
+      r = beor_set_schedule(ctxs, nsets, B, &s);
+      if (r) return r;
+      if (chosen) *chosen = s;
+      if (ms_chosen) *ms_chosen = m;
+      if (ms_default) *ms_default = md;
+      return BEOR_OK;
+    }
+  }
+  // candidates: the default first
+  int nsm = 0, dev_id = 0;
+  cudaGetDevice(&dev_id);
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess || nsm <= 0) {
+    cudaGetLastError();
+    nsm = 1;
+  }
+  std::vector<beor_schedule> cand;
+  if (beor::is_mixed(ctxs[0])) {
+    for (int align : {1, 0})
+      for (int cut : {0, 8, 16, 24}) {
+        if (cut >= nsm) continue;
+        cand.push_back(beor_schedule{1, cut ? nsm - cut : 0, 0, align});
+      }
+    for (int align : {1, 0}) cand.push_back(beor_schedule{0, 0, 0, align});
+  } else {
+    cand.push_back(beor_schedule{0, 0, 0, 1});
+  }
+  // outputs of the timed evaluations (host memory)
+  std::vector<std::vector<double>> lo(nsets);
+  std::vector<std::vector<int32_t>> so(nsets);
+  std::vector<double*> lp(nsets);
+  std::vector<int32_t*> sp(nsets);
+  for (int s = 0; s < nsets; ++s) {
+    lo[s].resize(B[s]);
+    so[s].resize(B[s]);
+    lp[s] = lo[s].data();
+    sp[s] = so[s].data();
+  }
+  double best = INFINITY, first = -1.0;
+  beor_schedule best_s = cand[0];
+  int last_err = BEOR_OK;
+  for (size_t c = 0; c < cand.size(); ++c) {
+    r = beor_set_schedule(ctxs, nsets, B, &cand[c]);
+    if (r) return r;
+    r = beor_lnl_multi(ctxs, nsets, phi, B, lp.data(), sp.data(), nullptr);   // builds, captures, runs once
+    if (r == BEOR_ENOMEM) {
+      last_err = r;
+      continue;
+    }
+    if (r) return r;
+    double t = INFINITY;
+    for (int i = 0; i < reps; ++i) {
+      r = beor_lnl_multi(ctxs, nsets, phi, B, lp.data(), sp.data(), nullptr);
+      if (r) return r;
+      beor_stats st{};
+      beor_get_stats(ctxs[0], &st);
+      if (st.ms_last > 0.0 && st.ms_last < t) t = st.ms_last;
+    }
+    if (c == 0) first = t;
+    if (t < best) {
+      best = t;
+      best_s = cand[c];
+    }
+  }
+  if (!std::isfinite(best)) {
+    beor_set_schedule(ctxs, nsets, B, &cur);
+    return last_err ? last_err : BEOR_ECUDA;
+  }
+  r = beor_set_schedule(ctxs, nsets, B, &best_s);
+  if (r) return r;
+  if (cache_path) write_entry(cache_path, dev, key, best_s, best, first);
+  if (chosen) *chosen = best_s;
+  if (ms_chosen) *ms_chosen = best;
+  if (ms_default) *ms_default = first;
+  return BEOR_OK;
+}

@@ -62,6 +62,9 @@ struct BatchView {
   // runs out and the error path is taken)
   unsigned long long wait_ns;
   int test_skip_copy;
+  // schedule: CTAs of the trailing launches for columns j >= k + 2 and of the
+  // next-column / panel launches (0: one per SM)
+  int grid_rest, grid_col;
 };
 
 // Launch with an explicit scheduling priority (0: the stream's own); the

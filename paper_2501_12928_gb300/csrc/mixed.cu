@@ -809,7 +809,8 @@ static int num_sms() {
 static cudaError_t launch_gemm(const BatchView& v, const MixedMaps* m, int k, int kind, cudaStream_t s, int prio) {
   const int64_t nt = m->h_total[kind][k];
   if (nt <= 0) return cudaSuccess;
-  const int grid = (int)std::min<int64_t>(nt, num_sms());
+  const int cap = kind == KIND_REST ? v.grid_rest : (kind == KIND_COL || kind == KIND_PANEL) ? v.grid_col : 0;
+  const int grid = (int)std::min<int64_t>(nt, cap > 0 ? cap : num_sms());
   const int64_t* pre = m->d_prefix + ((size_t)kind * m->max_nt + k) * (m->P + 1);
   int* ctr = m->d_counter + (size_t)kind * m->max_nt + k;
   if (kind == KIND_PANEL)
