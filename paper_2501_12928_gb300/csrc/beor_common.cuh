@@ -30,23 +30,32 @@
 __host__ __device__ __forceinline__ int slice_plane(int slice, int part) { return slice * BEOR_NPART + part; }
 
 // Tensor-core products of one A slice sa (0..4) with a two-part B window in
-// the slice GEMM.  Slice pair (sa, t) belongs to level min(sa + t, 3), pairs
-// with sa + t > 4 are dropped; the accumulators are four levels of 128 TMEM
-// columns, each a [re | im] pair of 64.  The window's slices t = 0..3-sa feed
-// levels sa..3, contiguous in TMEM and in the window, so they take one
-// product per two levels (N = 256 or 128); the pair t = 4 - sa adds into
-// level 3.  Product q < slice_mma_count(sa) reads the window from slice
-// slice_mma_t(sa, q) on, writes N = slice_mma_n(sa, q) columns from TMEM
+// the slice GEMM.  Slice pair (sa, t) belongs to level min(sa + t, 3); the
+// accumulators are four levels of 128 TMEM columns, each a [re | im] pair of
+// 64.  The window's slices t = 0..3-sa feed levels sa..3, contiguous in TMEM
+// and in the window, so they take one product per two levels (N = 256 or
+// 128, the `main` products).  The pair set is either
+//  * full: every pair with sa + t <= 4 -- the main products plus one extra
+//    product per slice for t = 4 - sa, into level 3; or
+//  * reduced: the pairs with sa + t <= 3 and (2, 2) -- the main products plus
+//    the extra one of slice 2.  The pairs dropped, (0, 4), (1, 3), (3, 1),
+//    (4, 0), lie 2^-32 below the leading term and have no sign bias off the
+//    diagonal; (2, 2) is kept, and tiles on the diagonal of a Hermitian
+//    product (P P^H, where |sigma_2|^2 >= 0 would bias the diagonal) use the
+//    full set.  Slice 4 is then never read.
+// Product q < slice_mma_count(sa, full) reads the window from slice
+// slice_mma_t(sa, q) on and writes N = slice_mma_n(sa, q) columns from TMEM
 // column slice_mma_col(sa, q).
-__host__ __device__ __forceinline__ int slice_mma_count(int sa) { return (5 - sa) / 2 + 1; }
-__host__ __device__ __forceinline__ int slice_mma_t(int sa, int q) {
-  return q + 1 < slice_mma_count(sa) ? 2 * q : 4 - sa;
+__host__ __device__ __forceinline__ int slice_mma_main(int sa) { return (5 - sa) / 2; }
+__host__ __device__ __forceinline__ int slice_mma_count(int sa, bool full) {
+  return slice_mma_main(sa) + ((full || sa == 2) ? 1 : 0);
 }
+__host__ __device__ __forceinline__ int slice_mma_t(int sa, int q) { return q < slice_mma_main(sa) ? 2 * q : 4 - sa; }
 __host__ __device__ __forceinline__ int slice_mma_col(int sa, int q) {
-  return q + 1 < slice_mma_count(sa) ? 128 * (sa + 2 * q) : 384;
+  return q < slice_mma_main(sa) ? 128 * (sa + 2 * q) : 384;
 }
 __host__ __device__ __forceinline__ int slice_mma_n(int sa, int q) {
-  if (q + 1 == slice_mma_count(sa)) return 128;
+  if (q >= slice_mma_main(sa)) return 128;
   const int left = 4 - sa - 2 * q;   // levels still to cover
   return 128 * (left < 2 ? left : 2);
 }

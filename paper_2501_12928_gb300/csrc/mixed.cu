@@ -75,6 +75,8 @@ struct MixedMaps {
   CUtensorMap panel_a[2];   // panel slices (two buffers by step parity), box: 128 rows x one K-chunk x 1 part x 5 slices
   CUtensorMap panel_b[2];   // the same, box 64 rows x 2 parts
   CUtensorMap linv_b;       // inverse-diagonal slices, box 64 rows x 2 parts
+  CUtensorMap panel_a4[2];  // as panel_a / panel_b, slices 0..3 only (off-diagonal trailing tiles)
+  CUtensorMap panel_b4[2];
   int64_t* d_prefix = nullptr;   // [4][max_nt][P+1] tile prefix sums (kinds col, rest, panel, all)
   int* d_counter = nullptr;      // [4][max_nt] dynamic tile counters, zeroed before every evaluation
   int max_nt = 0, P = 0;
@@ -279,9 +281,29 @@ __device__ __forceinline__ bool decode_tile(const BatchView& v, const int64_t* p
 // ---------------------------------------------------------------------------
 // the slice GEMM
 // ---------------------------------------------------------------------------
+// Products of one half-stage: every A slice with its B window (schedule
+// slice_mma_*, full or reduced pair set).  The first two products of a tile
+// (K-chunk 0, part Im, slice 0) cover all 512 columns and overwrite them.
+template <bool FULL>
+__device__ __forceinline__ void issue_half_stage(uint32_t tmem, uint32_t a0, uint32_t b0, bool first) {
+#pragma unroll
+  for (int sa = 0; sa < BEOR_NSLICE; ++sa) {
+    const uint64_t ad = sdesc_kmajor(a0 + sa * MX_SLICE_A);
+#pragma unroll
+    for (int q = 0; q < slice_mma_count(sa, FULL); ++q) {
+      const uint32_t acc = (first && sa == 0 && q < slice_mma_main(0)) ? 0u : 1u;
+      tc_mma(tmem + (uint32_t)slice_mma_col(sa, q), ad, sdesc_kmajor(b0 + slice_mma_t(sa, q) * MX_SLICE_B),
+             idesc_bf16(0, (uint32_t)slice_mma_n(sa, q)), acc);
+    }
+  }
+}
+
+// map_a / map_b: boxes of all 5 slices; map_a4 / map_b4: of slices 0..3, for
+// the trailing update's off-diagonal tiles (reduced pair set).
 template <int MODE>
 __global__ void __launch_bounds__(MX_THREADS, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                      const __grid_constant__ CUtensorMap map_a4, const __grid_constant__ CUtensorMap map_b4,
                       BatchView v, const int64_t* __restrict__ prefix, int64_t ntiles, int k, int kind,
                       int* __restrict__ counter, const int32_t* __restrict__ pexp) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -330,6 +352,10 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     prefetch_map(&map_a);
     prefetch_map(&map_b);
+    if (MODE == MODE_TRAIL) {
+      prefetch_map(&map_a4);
+      prefetch_map(&map_b4);
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
@@ -393,11 +419,19 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
               withheld = it;
               continue;
             }
-            mbar_expect_tx(full_bar(s), MX_HALF_BYTES);
             const uint32_t dst = sbase + s * MX_HALF_BYTES;
-            // x = 0 always (16-byte aligned); y counts pairs of 8-row groups
-            tma_load_5d(dst, &map_a, 0, a_row / 16, kc, h, 0, full_bar(s));
-            tma_load_5d(dst + MX_A_BYTES, &map_b, 0, b_row / 16, kc, h, 0, full_bar(s));
+            // x = 0 always (16-byte aligned); y counts pairs of 8-row groups.
+            // Off-diagonal trailing tiles never read slice 4 (reduced pair
+            // set): four-slice boxes, placed where the five-slice ones are.
+            if (MODE == MODE_TRAIL && jb.i != jb.j) {
+              mbar_expect_tx(full_bar(s), MX_HALF_BYTES * 4 / 5);
+              tma_load_5d(dst, &map_a4, 0, a_row / 16, kc, h, 0, full_bar(s));
+              tma_load_5d(dst + MX_A_BYTES, &map_b4, 0, b_row / 16, kc, h, 0, full_bar(s));
+            } else {
+              mbar_expect_tx(full_bar(s), MX_HALF_BYTES);
+              tma_load_5d(dst, &map_a, 0, a_row / 16, kc, h, 0, full_bar(s));
+              tma_load_5d(dst + MX_A_BYTES, &map_b, 0, b_row / 16, kc, h, 0, full_bar(s));
+            }
           }
         }
       }
@@ -442,19 +476,14 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
             // A slice sa times B slices t contributes to level min(sa + t, 3)
             // (schedule: slice_mma_*); the window's slices lie at 4 KB steps in
             // shared memory, their two parts 64 rows apart, so that a product
-            // over two levels reads 256 consecutive rows.  The first two
-            // products of a tile (K-chunk 0, part Im, slice 0) cover all 512
-            // columns and overwrite them.
-#pragma unroll
-            for (int sa = 0; sa < BEOR_NSLICE; ++sa) {
-              const uint64_t ad = sdesc_kmajor(a0 + sa * MX_SLICE_A);
-#pragma unroll
-              for (int q = 0; q < slice_mma_count(sa); ++q) {
-                const uint32_t acc = (kc == 0 && h == 0 && sa == 0 && q + 1 < slice_mma_count(sa)) ? 0u : 1u;
-                tc_mma(tmem + (uint32_t)slice_mma_col(sa, q), ad, sdesc_kmajor(b0 + slice_mma_t(sa, q) * MX_SLICE_B),
-                       idesc_bf16(0, (uint32_t)slice_mma_n(sa, q)), acc);
-              }
-            }
+            // over two levels reads 256 consecutive rows.  The panel product
+            // and the diagonal tiles of the trailing update take the full pair
+            // set, the other trailing tiles the reduced one.
+            const bool first = kc == 0 && h == 0;
+            if (MODE == MODE_PANEL || jb.i == jb.j)
+              issue_half_stage<true>(tmem, a0, b0, first);
+            else
+              issue_half_stage<false>(tmem, a0, b0, first);
             tc_commit(empty_bar(s));
           }
         }
@@ -708,7 +737,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 // K-chunk, `parts` consecutive parts from a given one and every slice is
 // exactly the shared-memory operand image (no swizzle), fetched as 512-byte
 // rows: [slice][part][rows] of 8-row x 16-byte core matrices.
-static cudaError_t make_map(CUtensorMap* m, void* base, int64_t rows, int box_rows, int parts) {
+static cudaError_t make_map(CUtensorMap* m, void* base, int64_t rows, int box_rows, int parts,
+                            int slices = BEOR_NSLICE) {
   auto enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
   if (rows % 16 || box_rows % 16) return cudaErrorInvalidValue;
@@ -716,7 +746,7 @@ static cudaError_t make_map(CUtensorMap* m, void* base, int64_t rows, int box_ro
                         (cuuint64_t)BEOR_NSLICE};
   cuuint64_t strides[4] = {512, (cuuint64_t)rows * MX_KC * 2, (cuuint64_t)rows * BEOR_TB * 2,
                            (cuuint64_t)rows * BEOR_TB * 2 * BEOR_NPART};
-  cuuint32_t box[5] = {256, (cuuint32_t)(box_rows / 16), 1, (cuuint32_t)parts, (cuuint32_t)BEOR_NSLICE};
+  cuuint32_t box[5] = {256, (cuuint32_t)(box_rows / 16), 1, (cuuint32_t)parts, (cuuint32_t)slices};
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -731,6 +761,8 @@ cudaError_t mixed_maps_create(const BatchView& v, MixedMaps** out) {
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
     e = make_map(&m->panel_a[b], slice_buf(v, b), v.rows, MX_M, 1);
     if (e == cudaSuccess) e = make_map(&m->panel_b[b], slice_buf(v, b), v.rows, MX_N, 2);
+    if (e == cudaSuccess) e = make_map(&m->panel_a4[b], slice_buf(v, b), v.rows, MX_M, 1, 4);
+    if (e == cudaSuccess) e = make_map(&m->panel_b4[b], slice_buf(v, b), v.rows, MX_N, 2, 4);
   }
   if (e == cudaSuccess) e = make_map(&m->linv_b, v.linv_sl, (int64_t)v.P * BEOR_TB, MX_N, 2);
   if (e != cudaSuccess) {
@@ -815,9 +847,11 @@ static cudaError_t launch_gemm(const BatchView& v, const MixedMaps* m, int k, in
   int* ctr = m->d_counter + (size_t)kind * m->max_nt + k;
   if (kind == KIND_PANEL)
     return launch_prio(slice_gemm_kernel<MODE_PANEL>, dim3(grid), dim3(MX_THREADS), (size_t)MX_SMEM, s, prio,
-                       m->panel_a[k & 1], m->linv_b, v, pre, nt, k, kind, ctr, (const int32_t*)exp_buf(v, k));
+                       m->panel_a[k & 1], m->linv_b, m->panel_a[k & 1], m->linv_b, v, pre, nt, k, kind, ctr,
+                       (const int32_t*)exp_buf(v, k));
   return launch_prio(slice_gemm_kernel<MODE_TRAIL>, dim3(grid), dim3(MX_THREADS), (size_t)MX_SMEM, s, prio,
-                     m->panel_a[k & 1], m->panel_b[k & 1], v, pre, nt, k, kind, ctr, (const int32_t*)exp_buf(v, k));
+                     m->panel_a[k & 1], m->panel_b[k & 1], m->panel_a4[k & 1], m->panel_b4[k & 1], v, pre, nt, k,
+                     kind, ctr, (const int32_t*)exp_buf(v, k));
 }
 
 cudaError_t launch_panel_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s, int prio) {

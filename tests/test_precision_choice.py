@@ -16,7 +16,12 @@ compared with the float64 factorisation of the same matrix:
   rounded to five balanced base-256 digits, products of digit slices (s, t)
   with s + t <= 4 summed in float64 (the tensor cores' fp32 accumulators are
   exact for them, or round far below 2^-40 of the result), panel and
-  trailing update alike.
+  trailing update alike;
+* the library's trailing update as it runs: the reduced pair set (s + t <= 3
+  and (2, 2)) on the off-diagonal tiles, the full set on the diagonal tiles
+  (128 x 128 blocks of P P^H) and in the panel product; and, to show why
+  the pair (2, 2) is kept, the pairs s + t <= 3 alone on every tile, which
+  drops the biased |sigma_2|^2 terms from the diagonal of P P^H.
 
 The likelihood's tolerance is |dlnL| <= 1e-2, i.e. 2e-2 in log|Sigma| (lnL
 carries -1/2 log|Sigma|; the quadratic form is corrected by a float64
@@ -77,17 +82,35 @@ def _digits(X):
     return e, [planes[0][s] + 1j * planes[1][s] for s in range(5)]
 
 
-def prod_slices(X, Y):
-    """X Y^H as the library's slice products: digit pairs s + t <= 4."""
+FULL = [(s, t) for s in range(5) for t in range(5) if s + t <= 4]
+LE3 = [(s, t) for s in range(5) for t in range(5) if s + t <= 3]
+REDUCED = LE3 + [(2, 2)]
+
+
+def prod_slices(X, Y, pairs=FULL):
+    """X Y^H as the library's slice products over the digit pairs (s, t) given."""
     ex, DX = _digits(X)
     ey, DY = _digits(Y)
     acc = np.zeros((X.shape[0], Y.shape[0]), np.complex128)
     for s in range(5):
-        # the slices t <= 4 - s of Y, summed exactly (40 bits); one product per s,
+        ts = [t for (a, t) in pairs if a == s]
+        if not ts:
+            continue
+        # the slices t of Y for this s, summed exactly (40 bits); one product per s,
         # exact but for float64 rounding (2^-53, far below the dropped pairs' 2^-40)
-        Yt = sum(DY[t] * 2.0 ** (-8 * t) for t in range(5 - s))
+        Yt = sum(DY[t] * 2.0 ** (-8 * t) for t in ts)
         acc += (DX[s] @ Yt.conj().T) * 2.0 ** (-8 * s)
     return acc * np.ldexp(1.0, ex - 7)[:, None] * np.ldexp(1.0, ey - 7)[None, :]
+
+
+def trail_library(P, Q, nb=128):
+    """The trailing update as the library runs it (P = Q = L_ik): reduced pair
+    set off the diagonal tiles, full set on them."""
+    U = prod_slices(P, Q, REDUCED)
+    for i0 in range(0, P.shape[0], nb):
+        i1 = min(i0 + nb, P.shape[0])
+        U[i0:i1, i0:i1] = prod_slices(P[i0:i1], Q[i0:i1], FULL)
+    return U
 
 
 def logdet_blocked(S, trail, panel, nb=128):
@@ -128,7 +151,7 @@ def test_split_tf32_misses_the_lnl_tolerance_and_slices_do_not():
     inst = build_instrument("C1")
     M = O.herm_structured(inst.A, inst.W, inst.noise_var)
     phis = draw_phi(inst.spec, 3)
-    tf32_err, slice_err = [], []
+    tf32_err, slice_err, lib_err, red_err = [], [], [], []
     for b, phi in enumerate(phis):
         pinv, _ = O.prior_diag(phi, inst.kbin, inst.spec.lssm_prior_var)
         S = M.copy()
@@ -137,9 +160,17 @@ def test_split_tf32_misses_the_lnl_tolerance_and_slices_do_not():
         tf32_err.append(abs(logdet_blocked(S, prod_tf32x3, exact) - ref))
         if b == 0:
             slice_err.append(abs(logdet_blocked(S, prod_slices, prod_slices) - ref))
-    print("log|Sigma| error, split TF32:", tf32_err, "slices:", slice_err)
+            lib_err.append(abs(logdet_blocked(S, trail_library, prod_slices) - ref))
+            red_err.append(logdet_blocked(S, lambda P, Q: prod_slices(P, Q, LE3), prod_slices) - ref)
+    print("log|Sigma| error, split TF32:", tf32_err, "slices:", slice_err, "library:", lib_err,
+          "s + t <= 3 on every tile (signed):", red_err)
     # every sampled point: split TF32 moves lnL by more than its tolerance
     assert min(tf32_err) > 2e-2
     # the slice products stay at least ten times inside it, and far below split TF32
     assert max(slice_err) < 2e-3
     assert min(tf32_err) > 10 * max(slice_err)
+    # the library's trailing pair sets stay at least four times inside the tolerance
+    assert max(lib_err) < 5e-3
+    # without (2, 2) each update subtracts too little from the diagonal
+    # (the dropped |sigma_2|^2 terms are never negative), so log|Sigma| rises
+    assert min(red_err) > 2e-2
