@@ -102,6 +102,43 @@ int beor_set_instrument(beor_ctx *ctx, const beor_c128 *A, const beor_c128 *W, i
                         int64_t ntb, int ncells, int nx, const int32_t *kbin, int n_k,
                         double lssm_prior_var);
 
+/* Instrument geometry (all host memory, copied).  Sec. "Running BayesEoR":
+ * the instrument model is the primary beam and the uv sampling. */
+typedef struct {
+  int nu;                        /* uv grid side, odd, 3..255: cells |i_u|, |i_v| <= (nu-1)/2, (0,0) removed */
+  int nf;                        /* frequency channels (= eta modes) */
+  int nf_grid;                   /* channels of the band that sets the uv cell (0 = nf): sub-bands of
+                                    one band pass the band's count so that they share its grid */
+  int n_lssm;                    /* foreground spectra (0..8) */
+  int n_pix;                     /* sky pixels per side (2..256) */
+  int n_bl, n_t, n_k;            /* baselines, time samples, k shells */
+  double f0_hz, df_hz;           /* channel f at f0 + f df */
+  double beam_fwhm_rad;          /* achromatic Gaussian primary beam */
+  double latitude_rad;           /* array latitude; drift scan pointed at the zenith */
+  double lssm_prior_var;         /* prior variance of every foreground amplitude */
+  const double *bl_enu_m;        /* n_bl x 3: east, north, up (metres) */
+  const double *hour_angle_rad;  /* n_t hour angles of the pointing */
+  const double *lssm_beta;       /* n_lssm spectral indices (may be NULL when n_lssm = 0) */
+} beor_instrument_desc;
+
+/* Builds the factored instrument from its geometry on the device and sets
+ * it as beor_set_instrument would: per channel f, A_f = NUDFT_f . diag(beam)
+ * . F_uv (the uv cells to an n_pix x n_pix sky grid by the unitary inverse
+ * 2-D DFT, the Gaussian beam, and each baseline / time sample's response
+ * exp(-2 pi i (u l + v m)) at its uv point in wavelengths at f), rows
+ * (t * n_bl + b); W = [E | S], E the unitary inverse eta-DFT over the
+ * channels (eta = -nf/2 .. nf/2 - 1), S the power laws (f/f0)^-beta, each
+ * column of unit 2-norm; model index j = c * (nf + n_lssm) + x, cells c
+ * with i_u fastest.  The uv cell du = (longest baseline at the top channel
+ * of nf_grid) / ((nu-1)/2), the sky grid spans 1 / du.  k bins: |k| =
+ * sqrt(i_u^2 + i_v^2 + eta^2) of the EoR modes, n_k log-spaced shells from
+ * the smallest to the largest |k| (k_i <= |k| < k_(i+1), the largest in the
+ * last shell); foreground modes -1.  Visibility index (f * n_t + t) * n_bl
+ * + b, so beor_set_data takes d and the noise in that order.  Errors:
+ * BEOR_EINVAL for sizes or values out of range, a zero-length baseline set,
+ * or an empty k shell; BEOR_ENOMEM. */
+int beor_set_instrument_desc(beor_ctx *ctx, const beor_instrument_desc *desc);
+
 /* Data vector d (n_vis complex) and noise variances (n_vis, all > 0): the
  * diagonal of N.  Host or device. */
 int beor_set_data(beor_ctx *ctx, const beor_c128 *d, const double *noise_var);

@@ -54,6 +54,7 @@ def _load():
         "beor_set_profiling": [_c.c_int],
         "beor_set_lookahead": [_c.c_int],
         "beor_set_wait_test": [_c.c_int, _c.c_double],
+        "beor_set_instrument_desc": [_P, _P],
         "beor_set_schedule": [_P, _c.c_int, _P, _P],
         "beor_get_schedule": [_P, _c.c_int, _P, _P],
         "beor_autotune": [_P, _c.c_int, _P, _P, _c.c_int, _c.c_char_p, _P, _P, _P],
@@ -114,6 +115,15 @@ def set_lookahead(on: bool):
 def set_wait_test(skip_one_copy: bool, limit_ms: float = 0.0):
     """Failure-detection test hook (see beor_set_wait_test); (False, 0) is the default."""
     _check(_lib().beor_set_wait_test(1 if skip_one_copy else 0, float(limit_ms)), "beor_set_wait_test")
+
+
+class InstrumentDesc(ctypes.Structure):
+    """beor_instrument_desc: the instrument's geometry (see include/beor.h)."""
+    _fields_ = [("nu", ctypes.c_int), ("nf", ctypes.c_int), ("nf_grid", ctypes.c_int), ("n_lssm", ctypes.c_int),
+                ("n_pix", ctypes.c_int), ("n_bl", ctypes.c_int), ("n_t", ctypes.c_int), ("n_k", ctypes.c_int),
+                ("f0_hz", ctypes.c_double), ("df_hz", ctypes.c_double), ("beam_fwhm_rad", ctypes.c_double),
+                ("latitude_rad", ctypes.c_double), ("lssm_prior_var", ctypes.c_double),
+                ("bl_enu_m", ctypes.c_void_p), ("hour_angle_rad", ctypes.c_void_p), ("lssm_beta", ctypes.c_void_p)]
 
 
 class Schedule(ctypes.Structure):
@@ -231,6 +241,22 @@ class Likelihood:
                                           nf, ntb, ncells, nx, _ptr(kbin, np.int32, keep), n_k,
                                           float(lssm_prior_var)), "beor_set_instrument")
         self.n_k = n_k
+
+    def set_instrument_desc(self, geometry: dict):
+        """Instrument built by the library from its geometry: a dict with the
+        beor_instrument_desc fields (arrays for bl_enu_m (n_bl x 3),
+        hour_angle_rad (n_t) and lssm_beta (n_lssm))."""
+        keep = []
+        g = dict(geometry)
+        bl = np.ascontiguousarray(g.pop("bl_enu_m"), np.float64)
+        ha = np.ascontiguousarray(g.pop("hour_angle_rad"), np.float64)
+        beta = np.ascontiguousarray(g.pop("lssm_beta", np.zeros(0)), np.float64)
+        keep += [bl, ha, beta]
+        desc = InstrumentDesc(n_bl=bl.shape[0], n_t=ha.shape[0], n_lssm=beta.shape[0],
+                              bl_enu_m=bl.ctypes.data, hour_angle_rad=ha.ctypes.data,
+                              lssm_beta=beta.ctypes.data if beta.size else None, **g)
+        _check(_lib().beor_set_instrument_desc(self._h, ctypes.byref(desc)), "beor_set_instrument_desc")
+        self.n_k = desc.n_k
 
     def set_data(self, d, noise_var):
         keep = []

@@ -14,5 +14,6 @@ from .instrument import (  # noqa: F401
     build_instrument,
     draw_phi,
     expand_T,
+    geometry,
     get_spec,
 )

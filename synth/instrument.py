@@ -271,6 +271,18 @@ def build_instrument(spec: InstrumentSpec | str, with_data: bool = True,
     return inst
 
 
+def geometry(inst: Instrument) -> dict:
+    """The instrument's geometry in the fields of the library's instrument
+    descriptor (beor_instrument_desc): from these the library builds the
+    same A_f, W and k-bin map as build_instrument."""
+    spec = inst.spec
+    return {"nu": spec.nu, "nf": spec.nf, "nf_grid": spec.nf_grid, "n_pix": spec.n_pix, "n_k": spec.n_k,
+            "f0_hz": spec.f0_hz, "df_hz": spec.df_hz, "beam_fwhm_rad": math.radians(spec.beam_fwhm_deg),
+            "latitude_rad": math.radians(LATITUDE_DEG), "lssm_prior_var": spec.lssm_prior_var,
+            "bl_enu_m": inst.bl_enu_m, "hour_angle_rad": inst.hour_angle_rad,
+            "lssm_beta": np.array(LSSM_BETAS[: spec.n_lssm], np.float64)}
+
+
 def bin_centres(edges: np.ndarray) -> np.ndarray:
     return np.sqrt(edges[:-1] * edges[1:])
 
