@@ -164,33 +164,56 @@ def train_emulator(phi, lnl, width=256, depth=4, seed=4, epochs=60, batch=1024, 
 
 
 class ActiveScreen:
-    """Emulator screen refit every `every` calls on all exact evaluations so
-    far (the initial set plus the sampler's own, which concentrate in the
-    shrinking constrained region), so that its support follows the run."""
+    """Emulator screen refit every `every` calls on the exact evaluations so
+    far, so that its support follows the run: the sampler's own evaluations
+    (which concentrate in the shrinking constrained region; the most recent
+    ones first) and a random part of the initial set, `max_train` points in
+    all.  `initial` is a ScreenModel to start from (not closed here); the
+    screen's own refits are."""
 
-    def __init__(self, exact: ExactLikelihood, phi0, lnl0, every=20, n_sigma=5.0, **train_kw):
+    def __init__(self, exact: ExactLikelihood, phi0, lnl0, every=20, n_sigma=5.0, max_train=None, initial=None,
+                 seed=0, **train_kw):
         self.exact = exact
-        self.phi, self.lnl = [phi0], [lnl0]
+        self.phi0, self.lnl0 = phi0, lnl0
+        self.run_phi, self.run_lnl = [], []
         self.every = every
         self.n_sigma = n_sigma
+        self.max_train = max_train
         self.train_kw = train_kw
+        self.rng = np.random.Generator(np.random.PCG64(seed))
         self.calls = 0
         self.refits = 0
-        self.model = None
-        self._refit()
+        self.refit_s = 0.0
+        self.model = initial
+        self.own = False
+        if initial is None:
+            self._refit()
+
+    def _training_set(self):
+        if self.exact.rec_x:
+            self.run_phi.append(np.concatenate(self.exact.rec_x))
+            self.run_lnl.append(np.concatenate(self.exact.rec_l))
+            self.exact.rec_x, self.exact.rec_l = [], []
+        rp = np.concatenate(self.run_phi) if self.run_phi else np.zeros((0, self.phi0.shape[1]))
+        rl = np.concatenate(self.run_lnl) if self.run_lnl else np.zeros(0)
+        if self.max_train is None:
+            return np.concatenate([self.phi0, rp]), np.concatenate([self.lnl0, rl])
+        keep_run = min(len(rl), (2 * self.max_train) // 3)
+        rp, rl = rp[len(rl) - keep_run:], rl[len(rl) - keep_run:]
+        n0 = min(len(self.lnl0), self.max_train - keep_run)
+        pick = self.rng.choice(len(self.lnl0), n0, replace=False)
+        return np.concatenate([self.phi0[pick], rp]), np.concatenate([self.lnl0[pick], rl])
 
     def _refit(self):
-        if self.exact.rec_x:
-            self.phi.append(np.concatenate(self.exact.rec_x))
-            self.lnl.append(np.concatenate(self.exact.rec_l))
-            self.exact.rec_x, self.exact.rec_l = [], []
-        phi = np.concatenate(self.phi)
-        lnl = np.concatenate(self.lnl)
+        t0 = time.perf_counter()
+        phi, lnl = self._training_set()
         ok = np.isfinite(lnl)
-        if self.model is not None:
+        model, _ = train_emulator(phi[ok], lnl[ok], seed=4 + self.refits, **self.train_kw)
+        if self.model is not None and self.own:
             self.model.em.close()
-        self.model, _ = train_emulator(phi[ok], lnl[ok], seed=4 + self.refits, **self.train_kw)
+        self.model, self.own = model, True
         self.refits += 1
+        self.refit_s += time.perf_counter() - t0
 
     @property
     def support_limit(self):
@@ -204,7 +227,7 @@ class ActiveScreen:
 
 
 def compare_runs_active(exact: ExactLikelihood, phi0, lnl0, n_k: int, n_live=500, k_remove=16, batch=64, seed=5,
-                        every=20, **train_kw):
+                        every=20, max_train=None, initial=None, **train_kw):
     """Seed-matched runs: exact likelihood only, and with an actively refit
     emulator screen (used while L_min lies below its current support limit).
     train_kw go to train_emulator (train_batch is its minibatch size)."""
@@ -215,8 +238,10 @@ def compare_runs_active(exact: ExactLikelihood, phi0, lnl0, n_k: int, n_live=500
         exact.n_points = 0
         flagged0, fallback0 = exact.n_flagged, exact.n_fallback
         exact.record = name == "emulator"
+        exact.rec_x, exact.rec_l = [], []
         t0 = time.perf_counter()
-        scr = ActiveScreen(exact, phi0, lnl0, every=every, **train_kw) if name == "emulator" else None
+        scr = (ActiveScreen(exact, phi0, lnl0, every=every, max_train=max_train, initial=initial, seed=seed,
+                            **train_kw) if name == "emulator" else None)
         ns = NestedSampler(exact, n_k, n_live=n_live, k_remove=k_remove, batch=batch, seed=seed, screen=scr,
                            screen_delta=0.0)
         ns._screen_owner = scr        # the support limit follows the refit model
@@ -224,8 +249,10 @@ def compare_runs_active(exact: ExactLikelihood, phi0, lnl0, n_k: int, n_live=500
         exact.record = False
         out[name] = {"logz": r.logz, "logz_err": r.logz_err, "h": r.h, "n_exact": r.n_exact,
                      "n_screened": r.n_screened, "n_iter": r.n_iter, "seconds": time.perf_counter() - t0,
-                     "refits": scr.refits if scr else 0, "n_flagged": exact.n_flagged - flagged0,
-                     "n_fallback": exact.n_fallback - fallback0}
+                     "refits": scr.refits if scr else 0, "refit_s": scr.refit_s if scr else 0.0,
+                     "n_flagged": exact.n_flagged - flagged0, "n_fallback": exact.n_fallback - fallback0}
+        if scr is not None and scr.own:
+            scr.model.em.close()
     out["dlogz"] = out["emulator"]["logz"] - out["exact"]["logz"]
     out["same_sequence"] = out["emulator"]["n_iter"] == out["exact"]["n_iter"] and abs(out["dlogz"]) < 1e-9
     out["exact_eval_ratio"] = out["emulator"]["n_exact"] / max(1, out["exact"]["n_exact"])
