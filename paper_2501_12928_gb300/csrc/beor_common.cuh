@@ -29,28 +29,40 @@
 #define BEOR_PART_NEGIM 2
 __host__ __device__ __forceinline__ int slice_plane(int slice, int part) { return slice * BEOR_NPART + part; }
 
-// Tensor-core products of one A slice sa (0..4) with a two-part B window in
-// the slice GEMM.  Slice pair (sa, t) belongs to level min(sa + t, 3); the
+// Tensor-core products of one A slice sa with a two-part B window in the
+// slice GEMMs.  Slice pair (sa, t) belongs to level min(sa + t, 3); the
 // accumulators are four levels of 128 TMEM columns, each a [re | im] pair of
 // 64.  The window's slices t = 0..3-sa feed levels sa..3, contiguous in TMEM
 // and in the window, so they take one product per two levels (N = 256 or
-// 128, the `main` products).  The pair set is either
-//  * full: every pair with sa + t <= 4 -- the main products plus one extra
-//    product per slice for t = 4 - sa, into level 3; or
-//  * reduced: the pairs with sa + t <= 3 and (2, 2) -- the main products plus
-//    the extra one of slice 2.  The pairs dropped, (0, 4), (1, 3), (3, 1),
-//    (4, 0), lie 2^-32 below the leading term and have no sign bias off the
-//    diagonal; (2, 2) is kept, and tiles on the diagonal of a Hermitian
-//    product (P P^H, where |sigma_2|^2 >= 0 would bias the diagonal) use the
-//    full set.  Slice 4 is then never read.
-// Product q < slice_mma_count(sa, full) reads the window from slice
-// slice_mma_t(sa, q) on and writes N = slice_mma_n(sa, q) columns from TMEM
-// column slice_mma_col(sa, q).
-__host__ __device__ __forceinline__ int slice_mma_main(int sa) { return (5 - sa) / 2; }
-__host__ __device__ __forceinline__ int slice_mma_count(int sa, bool full) {
-  return slice_mma_main(sa) + ((full || sa == 2) ? 1 : 0);
+// 128, the `main` products); every other pair of the set adds into level 3
+// with a product of its own (N = 128, the `extra` products).  Pair sets:
+//  * SLICE_PAIRS_FULL5 (5 slices): every pair with sa + t <= 4;
+//  * SLICE_PAIRS_REDUCED (5 slices, slice 4 unread): the pairs sa + t <= 3
+//    and (2, 2).  The pairs dropped, (0, 4), (1, 3), (3, 1), (4, 0), lie 2^-32
+//    below the leading term and have no sign bias off the diagonal; (2, 2)
+//    is kept, and tiles on the diagonal of a Hermitian product (P P^H, where
+//    |sigma_2|^2 >= 0 would bias the diagonal) use the full set;
+//  * SLICE_PAIRS_FULL7 (7 slices, 56-bit operands): every pair with
+//    sa + t <= 6; level 3 then rounds about 2^-48 below the leading term.
+// Product q < slice_mma_count(sa, set) reads the window from slice
+// slice_mma_t(sa, q, set) on and writes N = slice_mma_n(sa, q) columns from
+// TMEM column slice_mma_col(sa, q).
+enum { SLICE_PAIRS_REDUCED = 0, SLICE_PAIRS_FULL5 = 1, SLICE_PAIRS_FULL7 = 2 };
+__host__ __device__ __forceinline__ int slice_mma_main(int sa) { return sa <= 3 ? (5 - sa) / 2 : 0; }
+__host__ __device__ __forceinline__ int slice_mma_extra_first(int sa, int set) {
+  return set == SLICE_PAIRS_REDUCED ? 2 : (4 - sa > 0 ? 4 - sa : 0);
 }
-__host__ __device__ __forceinline__ int slice_mma_t(int sa, int q) { return q < slice_mma_main(sa) ? 2 * q : 4 - sa; }
+__host__ __device__ __forceinline__ int slice_mma_extras(int sa, int set) {
+  if (set == SLICE_PAIRS_REDUCED) return sa == 2 ? 1 : 0;
+  if (set == SLICE_PAIRS_FULL5) return sa <= 4 ? 1 : 0;
+  return sa <= 3 ? 3 : (sa <= 6 ? 7 - sa : 0);
+}
+__host__ __device__ __forceinline__ int slice_mma_count(int sa, int set) {
+  return slice_mma_main(sa) + slice_mma_extras(sa, set);
+}
+__host__ __device__ __forceinline__ int slice_mma_t(int sa, int q, int set) {
+  return q < slice_mma_main(sa) ? 2 * q : slice_mma_extra_first(sa, set) + (q - slice_mma_main(sa));
+}
 __host__ __device__ __forceinline__ int slice_mma_col(int sa, int q) {
   return q < slice_mma_main(sa) ? 128 * (sa + 2 * q) : 384;
 }

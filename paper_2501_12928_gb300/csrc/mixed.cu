@@ -133,16 +133,17 @@ __device__ __forceinline__ bool decode_tile(const BatchView& v, const int64_t* p
 // Products of one half-stage: every A slice with its B window (schedule
 // slice_mma_*, full or reduced pair set).  The first two products of a tile
 // (K-chunk 0, part Im, slice 0) cover all 512 columns and overwrite them.
-template <bool FULL>
+template <int SET>
 __device__ __forceinline__ void issue_half_stage(uint32_t tmem, uint32_t a0, uint32_t b0, bool first) {
 #pragma unroll
   for (int sa = 0; sa < BEOR_NSLICE; ++sa) {
     const uint64_t ad = sdesc_kmajor(a0 + sa * MX_SLICE_A);
 #pragma unroll
-    for (int q = 0; q < slice_mma_count(sa, FULL); ++q) {
+    for (int q = 0; q < slice_mma_count(sa, SET); ++q) {
       const uint32_t acc = (first && sa == 0 && q < slice_mma_main(0)) ? 0u : 1u;
-      tc_mma(tmem + (uint32_t)slice_mma_col(sa, q), ad, sdesc_kmajor(b0 + slice_mma_t(sa, q) * MX_SLICE_B),
-             idesc_bf16(0, (uint32_t)slice_mma_n(sa, q)), acc);
+      tc_mma(tmem + (uint32_t)slice_mma_col(sa, q), ad,
+             sdesc_kmajor(b0 + slice_mma_t(sa, q, SET) * MX_SLICE_B), idesc_bf16(0, (uint32_t)slice_mma_n(sa, q)),
+             acc);
     }
   }
 }
@@ -330,9 +331,9 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
             // set, the other trailing tiles the reduced one.
             const bool first = kc == 0 && h == 0;
             if (MODE == MODE_PANEL || jb.i == jb.j)
-              issue_half_stage<true>(tmem, a0, b0, first);
+              issue_half_stage<SLICE_PAIRS_FULL5>(tmem, a0, b0, first);
             else
-              issue_half_stage<false>(tmem, a0, b0, first);
+              issue_half_stage<SLICE_PAIRS_REDUCED>(tmem, a0, b0, first);
             tc_commit(empty_bar(s));
           }
         }

@@ -23,9 +23,10 @@ A second program emulates the schedule of tensor-core products
 (Im, Re), part Re with (Re, -Im)) on integer digits and checks that every
 level's [re | im] accumulator pair equals the complex product
 sum over the pairs (s, t) of the level of A_s B_t^H (level min(s + t, 3)),
-for the full pair set (s + t <= 4) and the reduced one (s + t <= 3 and
-(2, 2), slice 4 unread), with the first products of a tile overwriting and
-every later one accumulating.
+for the full pair set (s + t <= 4), the reduced one (s + t <= 3 and (2, 2),
+slice 4 unread) and the seven-slice set of the precompute (s + t <= 6),
+with the first products of a tile overwriting and every later one
+accumulating.
 """
 
 import os
@@ -101,72 +102,83 @@ SCHEDULE = r"""
 #include "beor_common.cuh"
 
 // Integer digits: A (m rows), B (64 rows), K = 3, real and imaginary parts
-// of 5 slices.  TMEM emulation: m lanes x 512 columns.
-int main() {
+// of ns slices; one pair set.  TMEM emulation: m lanes x 512 columns.
+static long long check(int ns, int set, int* nmma) {
   const int m = 4, nb = 64, K = 3;
-  long long A[2][BEOR_NSLICE][4][3], Bd[2][BEOR_NSLICE][64][3];   // [0] real, [1] imaginary
-  srand(7);
+  std::vector<long long> A(2 * ns * m * K), Bd(2 * ns * nb * K);   // [part 0 re, 1 im][slice][row][k]
+  auto a = [&](int p, int s, int r, int k) -> long long& { return A[((p * ns + s) * m + r) * K + k]; };
+  auto b = [&](int p, int s, int r, int k) -> long long& { return Bd[((p * ns + s) * nb + r) * K + k]; };
   for (int p = 0; p < 2; ++p)
-    for (int s = 0; s < BEOR_NSLICE; ++s) {
-      for (int r = 0; r < m; ++r) for (int k = 0; k < K; ++k) A[p][s][r][k] = rand() % 257 - 128;
-      for (int r = 0; r < nb; ++r) for (int k = 0; k < K; ++k) Bd[p][s][r][k] = rand() % 257 - 128;
+    for (int s = 0; s < ns; ++s) {
+      for (int r = 0; r < m; ++r) for (int k = 0; k < K; ++k) a(p, s, r, k) = rand() % 257 - 128;
+      for (int r = 0; r < nb; ++r) for (int k = 0; k < K; ++k) b(p, s, r, k) = rand() % 257 - 128;
     }
+  auto in_set = [&](int s, int t) {
+    if (set == SLICE_PAIRS_REDUCED) return s + t <= 3 || (s == 2 && t == 2);
+    if (set == SLICE_PAIRS_FULL5) return s + t <= 4;
+    return s + t <= 6;
+  };
   // B planes in the library's part order
   auto bplane = [&](int s, int part, int r, int k) -> long long {
-    if (part == BEOR_PART_RE) return Bd[0][s][r][k];
-    if (part == BEOR_PART_IM) return Bd[1][s][r][k];
-    if (part == BEOR_PART_NEGIM) return -Bd[1][s][r][k];
+    if (part == BEOR_PART_RE) return b(0, s, r, k);
+    if (part == BEOR_PART_IM) return b(1, s, r, k);
+    if (part == BEOR_PART_NEGIM) return -b(1, s, r, k);
     return 1LL << 40;
   };
-  long long bad = 0;
-  int nmma[2] = {0, 0};
-  for (int full = 0; full < 2; ++full) {
   std::vector<long long> T((size_t)m * 512, 777);   // stale contents must be overwritten
   std::vector<int> written(512, 0);
+  long long bad = 0;
+  *nmma = 0;
+  for (int sa = 0; sa < ns; ++sa) *nmma += slice_mma_count(sa, set);
   for (int kc = 0; kc < 2; ++kc)
     for (int h = 0; h < 2; ++h) {
       const int apart = h == 0 ? 1 : 0;            // half-stage 0: A part Im, 1: A part Re
       const int p0 = h == 0 ? BEOR_PART_IM : BEOR_PART_RE;
-      for (int sa = 0; sa < BEOR_NSLICE; ++sa)
-        for (int q = 0; q < slice_mma_count(sa, full); ++q) {
+      for (int sa = 0; sa < ns; ++sa)
+        for (int q = 0; q < slice_mma_count(sa, set); ++q) {
           const bool acc = !(kc == 0 && h == 0 && sa == 0 && q < slice_mma_main(0));
-          const int col = slice_mma_col(sa, q), t0 = slice_mma_t(sa, q), n = slice_mma_n(sa, q);
+          const int col = slice_mma_col(sa, q), t0 = slice_mma_t(sa, q, set), n = slice_mma_n(sa, q);
           if (col + n > 512 || n % 128 || n > 256 || n < 128) ++bad;
           for (int j = 0; j < n; ++j) {
             const int t = t0 + j / 128, part = p0 + (j / 64) % 2, br = j % 64;
-            if (t >= BEOR_NSLICE || (!full && (t == 4 || sa == 4))) { ++bad; continue; }
+            if (t >= ns || !in_set(sa, t)) { ++bad; continue; }
             if (!acc) written[col + j] = 1;
             else if (!written[col + j]) ++bad;           // accumulating into a column never overwritten
             for (int r = 0; r < m; ++r) {
               long long v = 0;
-              for (int k = 0; k < K; ++k) v += A[apart][sa][r][k] * bplane(t, part, br, k);
+              for (int k = 0; k < K; ++k) v += a(apart, sa, r, k) * bplane(t, part, br, k);
               long long& d = T[(size_t)r * 512 + col + j];
               d = acc ? d + v : v;
             }
           }
         }
     }
-  // expected: level l, re = sum Ar Br + Ai Bi, im = sum Ai Br - Ar Bi over pairs in the level
-  // (twice: two K-chunks of the same data)
+  // expected: level l, re = sum Ar Br + Ai Bi, im = sum Ai Br - Ar Bi over the set's pairs of
+  // the level (twice: two K-chunks of the same data); every pair of the set is covered once
   for (int l = 0; l < 4; ++l)
     for (int r = 0; r < m; ++r)
       for (int c = 0; c < nb; ++c) {
         long long re = 0, im = 0;
-        for (int s = 0; s < BEOR_NSLICE; ++s)
-          for (int t = 0; t < BEOR_NSLICE; ++t) {
-            const bool in_set = full ? s + t <= 4 : (s + t <= 3 || (s == 2 && t == 2));
-            if (!in_set || (s + t < 3 ? s + t : 3) != l) continue;
+        for (int s = 0; s < ns; ++s)
+          for (int t = 0; t < ns; ++t) {
+            if (!in_set(s, t) || (s + t < 3 ? s + t : 3) != l) continue;
             for (int k = 0; k < K; ++k) {
-              re += A[0][s][r][k] * Bd[0][t][c][k] + A[1][s][r][k] * Bd[1][t][c][k];
-              im += A[1][s][r][k] * Bd[0][t][c][k] - A[0][s][r][k] * Bd[1][t][c][k];
+              re += a(0, s, r, k) * b(0, t, c, k) + a(1, s, r, k) * b(1, t, c, k);
+              im += a(1, s, r, k) * b(0, t, c, k) - a(0, s, r, k) * b(1, t, c, k);
             }
           }
         bad += T[(size_t)r * 512 + 128 * l + c] != 2 * re;
         bad += T[(size_t)r * 512 + 128 * l + 64 + c] != 2 * im;
       }
-  for (int sa = 0; sa < BEOR_NSLICE; ++sa) nmma[full] += slice_mma_count(sa, full);
-  }
-  std::printf("mismatches %lld products per half-stage %d (full) %d (reduced)\n", bad, nmma[1], nmma[0]);
+  return bad;
+}
+
+int main() {
+  srand(7);
+  int n5 = 0, nr = 0, n7 = 0;
+  long long bad = check(5, SLICE_PAIRS_FULL5, &n5) + check(5, SLICE_PAIRS_REDUCED, &nr) +
+                  check(7, SLICE_PAIRS_FULL7, &n7);
+  std::printf("mismatches %lld products per half-stage %d (full) %d (reduced) %d (7 slices)\n", bad, n5, nr, n7);
   return bad != 0;
 }
 """
@@ -193,4 +205,4 @@ def test_slice_planes_match_tma_boxes_and_core_matrices(tmp_path):
 def test_product_schedule_gives_each_level_its_complex_product(tmp_path):
     r = _build_run(tmp_path, "schedule", SCHEDULE)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert "mismatches 0 products per half-stage 11 (full) 7 (reduced)" in r.stdout
+    assert "mismatches 0 products per half-stage 11 (full) 7 (reduced) 24 (7 slices)" in r.stdout
