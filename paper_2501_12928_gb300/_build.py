@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libbeor.so")
-SOURCES = ["api.cu", "precompute.cu", "chol.cu", "mixed.cu", "mlp.cu", "noalloc.cu", "autotune.cu", "instrument.cu"]
+SOURCES = ["api.cu", "precompute.cu", "chol.cu", "mixed.cu", "mlp.cu", "noalloc.cu", "autotune.cu", "instrument.cu", "herk_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -726,7 +726,7 @@ int beor_precompute(beor_ctx* c, void* stream) {
   CKC(c, c->dbar.alloc(sizeof(double2) * (size_t)c->nt * BEOR_TB));
   if (c->model_kind == 1) {
     CKC(c, precompute_dense(c->T.as<double2>(), c->n_vis, c->n, c->ld, c->w.as<double>(), c->d.as<double2>(), c->nt,
-                            c->M.as<double2>(), c->dbar.as<double2>(), s));
+                            c->M.as<double2>(), c->dbar.as<double2>(), s, c->precision == BEOR_PREC_MIXED));
   } else {
     DevBuf G, u;
     CKC(c, G.alloc(sizeof(double2) * (size_t)c->nf * c->ncells * c->ncells));

@@ -16,7 +16,10 @@ cudaError_t split_double_float(const double2* M, int64_t n, float4* out, cudaStr
 // element split exactly into three floats per component.
 cudaError_t split_full_triple(const double2* M, int n, int nt, float4* hl, float2* t, cudaStream_t s);
 cudaError_t precompute_dense(const double2* T, int64_t n_vis, int n, int64_t ld, const double* w,
-                             const double2* d, int nt, double2* Mt, double2* dbar, cudaStream_t s);
+                             const double2* d, int nt, double2* Mt, double2* dbar, cudaStream_t s, bool tc);
+// herk_tc.cu: M (packed lower float64 tiles) = T^H diag(w) T on the tensor cores
+cudaError_t herk_dense_tc(const double2* T, int64_t n_vis, int n, int64_t ld, const double* w, int nt,
+                          double2* Mt, cudaStream_t s);
 cudaError_t precompute_factored(const double2* A, const double2* W, int nf, int64_t ntb, int ncells,
                                 int nx, const double* w, const double2* d, int n, int nt,
                                 double2* G_scratch, double2* u_scratch, double2* Mt, double2* dbar,

@@ -4,7 +4,9 @@
 // likelihood needs the data-space products T^H N^-1 T and T^H N^-1 d once
 // per instrument, after which every prior point only changes a diagonal.
 // Two routes:
-//  * dense:    M = T^H diag(w) T directly from T (n_vis x n row-major),
+//  * dense:    M = T^H diag(w) T directly from T (n_vis x n row-major): on
+//              the FP64 pipe (float64 contexts) or as seven-digit bf16 slice
+//              products on the tensor cores (mixed contexts, herk_tc.cu),
 //  * factored: T[(f,tb),(c,x)] = A_f[tb,c] W[f,x] gives
 //              G_f = A_f^H diag(w_f) A_f and
 //              M[(c,x),(c',x')] = sum_f conj(W[f,x]) W[f,x'] G_f[c,c'],
@@ -235,10 +237,15 @@ cudaError_t split_double_float(const double2* M, int64_t n, float4* out, cudaStr
 
 // ---------------------------------------------------------------------------
 cudaError_t precompute_dense(const double2* T, int64_t n_vis, int n, int64_t ld, const double* w,
-                             const double2* d, int nt, double2* Mt, double2* dbar, cudaStream_t s) {
-  dim3 grid((unsigned)(tri_count(nt) * 4), 1, 1);
-  herk_f64_kernel<<<grid, 256, 0, s>>>(T, ld, 0, w, 0, n_vis, n, nt, Mt, 0, 0, 0);
-  cudaError_t e = cudaGetLastError();
+                             const double2* d, int nt, double2* Mt, double2* dbar, cudaStream_t s, bool tc) {
+  cudaError_t e;
+  if (tc) {
+    e = herk_dense_tc(T, n_vis, n, ld, w, nt, Mt, s);   // seven-digit slice products (herk_tc.cu)
+  } else {
+    dim3 grid((unsigned)(tri_count(nt) * 4), 1, 1);
+    herk_f64_kernel<<<grid, 256, 0, s>>>(T, ld, 0, w, 0, n_vis, n, nt, Mt, 0, 0, 0);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   cudaMemsetAsync(dbar, 0, sizeof(double2) * (size_t)nt * BEOR_TB, s);
   int64_t kchunk = 4096;

@@ -123,9 +123,16 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float* v) {
+  uint32_t r[2];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+  v[0] = __uint_as_float(r[0]);
+  v[1] = __uint_as_float(r[1]);
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 // Pins four registers written by tcgen05.ld after the wait that completes the
 // load, so that no use of them is scheduled before it.
+__device__ __forceinline__ void reg_fence2(float* v) { asm volatile("" : "+f"(v[0]), "+f"(v[1])); }
 __device__ __forceinline__ void reg_fence4(float* v) {
   asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]));
 }
