@@ -82,6 +82,9 @@ def main(argv=None):
         res.append(r)
         print(json.dumps({"seed": sd, "dlogz": r["dlogz"], "exact_eval_ratio": r["exact_eval_ratio"],
                           "n_exact": [r["exact"]["n_exact"], r["emulator"]["n_exact"]]}), flush=True)
+        if args.out:   # the pairs so far, in case the run is cut short
+            with open(args.out + ".partial", "w") as f:
+                f.write(json.dumps({**out, "runs": res}, default=float) + "\n")
     d = np.array([r["dlogz"] for r in res])
     q = np.array([r["exact_eval_ratio"] for r in res])
     out["summary"] = {"pairs": len(res), "dlogz_mean": float(d.mean()), "dlogz_std": float(d.std()),

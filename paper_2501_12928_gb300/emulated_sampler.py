@@ -164,8 +164,10 @@ def train_emulator(phi, lnl, width=256, depth=4, seed=4, epochs=60, batch=1024, 
 
 
 class ActiveScreen:
-    """Emulator screen refit every `every` calls on the exact evaluations so
-    far, so that its support follows the run: the sampler's own evaluations
+    """Emulator screen refit every `every` candidate blocks of the sampler
+    (tick(), called for every block, screened or not, so that the support
+    limit keeps up with L_min) on the exact evaluations so far, so that its
+    support follows the run: the sampler's own evaluations
     (which concentrate in the shrinking constrained region; the most recent
     ones first) and a random part of the initial set, `max_train` points in
     all.  `initial` is a ScreenModel to start from (not closed here); the
@@ -219,10 +221,12 @@ class ActiveScreen:
     def support_limit(self):
         return self.model.support_limit
 
-    def __call__(self, cand):
+    def tick(self):
         self.calls += 1
         if self.calls % self.every == 0:
             self._refit()
+
+    def __call__(self, cand):
         return self.model.screen(self.n_sigma * self.model.rms_u)(cand)
 
 

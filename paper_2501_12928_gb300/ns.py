@@ -19,8 +19,10 @@ uncertainty, weighted posterior samples):
 * with an emulator, a candidate whose predicted lnL is below L_min - delta is
   skipped without an exact evaluation, but only while L_min is below
   `screen_limit` (the range where the emulator's training data give it
-  support); every accepted point, and therefore the evidence, uses the exact
-  likelihood;
+  support); an adaptive screen (`_screen_owner`, with `tick()` and
+  `support_limit`) is told of every candidate block, so that it can refit
+  and move its support limit while it is not consulted; every accepted
+  point, and therefore the evidence, uses the exact likelihood;
 * the run stops when the live points can add less than `stop_frac` of the
   current evidence, then the live points are added.
 
@@ -119,9 +121,12 @@ class NestedSampler:
         """`need` accepted points with exact lnL > lmin, in draw order."""
         acc_x, acc_l = [], []
         empty = 0
+        owner = getattr(self, "_screen_owner", None)
         while len(acc_x) < need:
             cand = self._draw_block(mu, chol, self.batch)
-            limit = getattr(getattr(self, "_screen_owner", None), "support_limit", self.screen_limit)
+            if owner is not None:
+                owner.tick()          # an adaptive screen updates itself on every block, screened or not
+            limit = getattr(owner, "support_limit", self.screen_limit)
             if self.screen is not None and lmin < limit and empty < self.max_empty_blocks:
                 pred = np.asarray(self.screen(cand), float)
                 keep = pred >= lmin - self.delta

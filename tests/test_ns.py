@@ -70,3 +70,34 @@ def test_checkpoint_resume(tmp_path):
     assert resumed.n_iter == full.n_iter
     assert abs(resumed.logz - full.logz) < 1e-9
     assert resumed.n_exact == full.n_exact
+
+
+def test_adaptive_screen_is_ticked_on_every_block():
+    """An adaptive screen must hear of every candidate block, also while L_min
+    is above its support limit (else it could never move that limit)."""
+    import math
+
+    from paper_2501_12928_gb300.ns import NestedSampler
+
+    class Owner:
+        def __init__(self):
+            self.ticks = 0
+            self.support_limit = -math.inf     # never consulted
+
+        def tick(self):
+            self.ticks += 1
+
+    calls = []
+
+    def loglike(x):
+        calls.append(len(x))
+        return -0.5 * np.sum(np.asarray(x) ** 2, axis=1)
+
+    owner = Owner()
+    ns = NestedSampler(loglike, 2, n_live=40, k_remove=4, batch=16, seed=3, screen=lambda c: np.zeros(len(c)),
+                       max_iter=30)
+    ns._screen_owner = owner
+    ns.run()
+    blocks = len(calls) - math.ceil(40 / 16)     # the initial live points come in ceil(40/16) calls
+    assert owner.ticks == blocks > 0
+    assert ns.n_screened == 0
