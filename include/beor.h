@@ -270,12 +270,17 @@ int beor_set_lookahead(int on);
  *   col_ctas:   the same for the next-column update and the panel product.
  *   align_ends: 1 = in a batch of uneven sizes, smaller problems start late
  *               so that all end on the last block step (their light final
- *               steps overlap); 0 = all start on step 0. */
+ *               steps overlap); 0 = all start on step 0.
+ *   reserve_diag: 1 = each launch for columns j >= k + 2 also leaves free as
+ *               many SMs as step k + 1 has diagonal blocks (one CTA per
+ *               problem, running beside it at high priority), so that they
+ *               start at once; 0 = no such reserve. */
 typedef struct {
   int lookahead;
   int rest_ctas;
   int col_ctas;
   int align_ends;
+  int reserve_diag;
 } beor_schedule;
 
 /* Set (sch != NULL) or reset to the default (NULL) the schedule of lnL
@@ -293,8 +298,9 @@ int beor_get_schedule(beor_ctx *const *ctxs, int n_sets, const int *B, beor_sche
  * beor_lnl_multi).  If cache_path names a file holding an entry for this
  * device and shape, that schedule is applied and returned without timing.
  * Otherwise every candidate -- look-ahead on with rest_ctas in {one per SM,
- * 8, 16, 24 fewer} and align_ends in {1, 0}, and look-ahead off with
- * align_ends in {1, 0} -- is applied and timed: one untimed evaluation
+ * 8, 16, 24 fewer}, align_ends in {1, 0} and reserve_diag in {0, 1}, and
+ * look-ahead off with align_ends in {1, 0} -- is applied and timed: one
+ * untimed evaluation
  * (building the batch and its graph), then `reps` evaluations (1..100),
  * the fastest device time counting.  The fastest candidate is applied
  * (beor_set_schedule) and, with cache_path, appended to the cache (one JSON

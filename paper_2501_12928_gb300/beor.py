@@ -128,9 +128,9 @@ class InstrumentDesc(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     """beor_schedule: look-ahead, CTAs of the rest / next-column launches
-    (0 = one per SM), aligned ends."""
+    (0 = one per SM), aligned ends, SMs reserved for the diagonal blocks."""
     _fields_ = [("lookahead", ctypes.c_int), ("rest_ctas", ctypes.c_int), ("col_ctas", ctypes.c_int),
-                ("align_ends", ctypes.c_int)]
+                ("align_ends", ctypes.c_int), ("reserve_diag", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -255,7 +255,18 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
       RUN_ON(KC_SOLVE, pl.side2, launch_fwd_step(v, true, v.vec_b, k, pl.side2));
       L += 1;
       if (mixed_tiles(pl.maps, 1, k) > 0) {
-        RUN_ON(KC_TRAIL, pl.side, launch_trail_mixed(v, pl.maps, k, TRAIL_REST, pl.side));
+        // reserve_diag: leave free the SMs that step k + 1's diagonal blocks
+        // (one CTA each, running beside this launch) need
+        int cap = 0;
+        if (pl.sch.reserve_diag) {
+          int active = 0;
+          for (const Prob& pr : pl.h_prob) {
+            const int kp = k + 1 - pr.k_off;
+            active += kp >= 0 && kp < pr.nt && pr.n > 0;
+          }
+          cap = std::max(8, device_sms() - active);
+        }
+        RUN_ON(KC_TRAIL, pl.side, launch_trail_mixed(v, pl.maps, k, TRAIL_REST, pl.side, 0, cap));
         L += 1;
       }
       if ((e = cudaEventRecord(pl.ev_rest, pl.side)) != cudaSuccess) return e;
@@ -335,6 +346,7 @@ beor_schedule default_schedule() {
   d.rest_ctas = 0;
   d.col_ctas = 0;
   d.align_ends = 1;
+  d.reserve_diag = 0;
   return d;
 }
 
@@ -345,7 +357,7 @@ beor_schedule schedule_of(const std::string& key) {
 
 bool same_schedule(const beor_schedule& a, const beor_schedule& b) {
   return a.lookahead == b.lookahead && a.rest_ctas == b.rest_ctas && a.col_ctas == b.col_ctas &&
-         a.align_ends == b.align_ends;
+         a.align_ends == b.align_ends && a.reserve_diag == b.reserve_diag;
 }
 
 int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, int slot, Plan** out) {
@@ -1068,6 +1080,7 @@ int beor_set_schedule(beor_ctx* const* ctxs, int nsets, const int* B, const beor
     beor_schedule c = *sch;
     c.lookahead = c.lookahead != 0;
     c.align_ends = c.align_ends != 0;
+    c.reserve_diag = c.reserve_diag != 0;
     g_schedules[key] = c;
   } else {
     g_schedules.erase(key);

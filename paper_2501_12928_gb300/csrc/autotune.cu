@@ -70,10 +70,10 @@ bool read_entry(const char* path, const std::string& dev, const std::string& key
     if (!json_field(line, "device", &d) || !json_field(line, "shape", &k) || d != dev || k != key) continue;
     beor_schedule s{};
     double m = -1.0, md = -1.0;
-    int* fields[4] = {&s.lookahead, &s.rest_ctas, &s.col_ctas, &s.align_ends};
-    const char* names[4] = {"lookahead", "rest_ctas", "col_ctas", "align_ends"};
+    int* fields[5] = {&s.lookahead, &s.rest_ctas, &s.col_ctas, &s.align_ends, &s.reserve_diag};
+    const char* names[5] = {"lookahead", "rest_ctas", "col_ctas", "align_ends", "reserve_diag"};
     bool ok = true;
-    for (int q = 0; q < 4 && ok; ++q) {
+    for (int q = 0; q < 5 && ok; ++q) {
       ok = json_field(line, names[q], &v);
       if (ok) *fields[q] = std::atoi(v.c_str());
     }
@@ -95,8 +95,9 @@ void write_entry(const char* path, const std::string& dev, const std::string& ke
   if (!f) return;
   std::fprintf(f,
                "{\"device\": \"%s\", \"shape\": \"%s\", \"lookahead\": %d, \"rest_ctas\": %d, \"col_ctas\": %d, "
-               "\"align_ends\": %d, \"ms\": %.4f, \"ms_default\": %.4f}\n",
-               dev.c_str(), key.c_str(), s.lookahead, s.rest_ctas, s.col_ctas, s.align_ends, ms, ms_default);
+               "\"align_ends\": %d, \"reserve_diag\": %d, \"ms\": %.4f, \"ms_default\": %.4f}\n",
+               dev.c_str(), key.c_str(), s.lookahead, s.rest_ctas, s.col_ctas, s.align_ends, s.reserve_diag, ms,
+               ms_default);
   std::fclose(f);
 }
 
@@ -134,14 +135,15 @@ extern "C" int beor_autotune(beor_ctx* const* ctxs, int nsets, const double* con
   }
   std::vector<beor_schedule> cand;
   if (beor::is_mixed(ctxs[0])) {
-    for (int align : {1, 0})
-      for (int cut : {0, 8, 16, 24}) {
-        if (cut >= nsm) continue;
-        cand.push_back(beor_schedule{1, cut ? nsm - cut : 0, 0, align});
-      }
-    for (int align : {1, 0}) cand.push_back(beor_schedule{0, 0, 0, align});
+    for (int reserve : {0, 1})
+      for (int align : {1, 0})
+        for (int cut : {0, 8, 16, 24}) {
+          if (cut >= nsm) continue;
+          cand.push_back(beor_schedule{1, cut ? nsm - cut : 0, 0, align, reserve});
+        }
+    for (int align : {1, 0}) cand.push_back(beor_schedule{0, 0, 0, align, 0});
   } else {
-    cand.push_back(beor_schedule{0, 0, 0, 1});
+    cand.push_back(beor_schedule{0, 0, 0, 1, 0});
   }
   // outputs of the timed evaluations (host memory)
   std::vector<std::vector<double>> lo(nsets);

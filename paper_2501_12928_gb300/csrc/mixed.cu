@@ -688,11 +688,14 @@ static int num_sms() {
   return n;
 }
 
-static cudaError_t launch_gemm(const BatchView& v, const MixedMaps* m, int k, int kind, cudaStream_t s, int prio) {
+static cudaError_t launch_gemm(const BatchView& v, const MixedMaps* m, int k, int kind, cudaStream_t s, int prio,
+                               int max_ctas = 0) {
   const int64_t nt = m->h_total[kind][k];
   if (nt <= 0) return cudaSuccess;
-  const int cap = kind == KIND_REST ? v.grid_rest : (kind == KIND_COL || kind == KIND_PANEL) ? v.grid_col : 0;
-  const int grid = (int)std::min<int64_t>(nt, cap > 0 ? cap : num_sms());
+  int cap = kind == KIND_REST ? v.grid_rest : (kind == KIND_COL || kind == KIND_PANEL) ? v.grid_col : 0;
+  if (cap <= 0) cap = num_sms();
+  if (max_ctas > 0) cap = std::min(cap, max_ctas);
+  const int grid = (int)std::min<int64_t>(nt, cap);
   const int64_t* pre = m->d_prefix + ((size_t)kind * m->max_nt + k) * (m->P + 1);
   int* ctr = m->d_counter + (size_t)kind * m->max_nt + k;
   if (kind == KIND_PANEL)
@@ -708,10 +711,13 @@ cudaError_t launch_panel_mixed(const BatchView& v, const MixedMaps* m, int k, cu
   return launch_gemm(v, m, k, KIND_PANEL, s, prio);
 }
 
-cudaError_t launch_trail_mixed(const BatchView& v, const MixedMaps* m, int k, int part, cudaStream_t s, int prio) {
+cudaError_t launch_trail_mixed(const BatchView& v, const MixedMaps* m, int k, int part, cudaStream_t s, int prio,
+                               int max_ctas) {
   const int kind = part == TRAIL_NEXT_COL ? KIND_COL : part == TRAIL_REST ? KIND_REST : KIND_ALL;
-  return launch_gemm(v, m, k, kind, s, prio);
+  return launch_gemm(v, m, k, kind, s, prio, max_ctas);
 }
+
+int device_sms() { return num_sms(); }
 
 // ---------------------------------------------------------------------------
 // float64 refinement: vec_r = dbar - (M + diag Phi^-1) x, x += vec_d

@@ -63,10 +63,11 @@ def test_every_schedule_gives_the_same_factor():
     likes = [make_like(P, "C0", "mixed"), make_like(P, "C1", "mixed")]
     ph = [phis("C0", 2, stream=5), phis("C1", 2, stream=5)]
     Bs = [2, 2]
-    scheds = [dict(lookahead=1, rest_ctas=0, col_ctas=0, align_ends=1),
-              dict(lookahead=1, rest_ctas=100, col_ctas=37, align_ends=0),
-              dict(lookahead=0, rest_ctas=0, col_ctas=0, align_ends=0),
-              dict(lookahead=0, rest_ctas=64, col_ctas=5, align_ends=1)]
+    scheds = [dict(lookahead=1, rest_ctas=0, col_ctas=0, align_ends=1, reserve_diag=0),
+              dict(lookahead=1, rest_ctas=100, col_ctas=37, align_ends=0, reserve_diag=0),
+              dict(lookahead=1, rest_ctas=0, col_ctas=0, align_ends=1, reserve_diag=1),
+              dict(lookahead=0, rest_ctas=0, col_ctas=0, align_ends=0, reserve_diag=0),
+              dict(lookahead=0, rest_ctas=64, col_ctas=5, align_ends=1, reserve_diag=1)]
     try:
         facs, dets = [], []
         for sc in scheds:
