@@ -412,6 +412,10 @@ int beor_mlp_grad(beor_mlp *mlp, const float *x, const float *y, int n, int laye
 
 const char *beor_strerror(int code);
 
+/* Name of the CUDA error behind the calling thread's last BEOR_ECUDA or
+ * BEOR_ENOMEM ("cudaSuccess" if none). */
+const char *beor_last_cuda_error(void);
+
 #ifdef __cplusplus
 }
 #endif

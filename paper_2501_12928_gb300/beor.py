@@ -74,6 +74,8 @@ def _load():
         f.restype = _c.c_int
     L.beor_strerror.argtypes = [_c.c_int]
     L.beor_strerror.restype = _c.c_char_p
+    L.beor_last_cuda_error.argtypes = []
+    L.beor_last_cuda_error.restype = _c.c_char_p
     return L
 
 
@@ -90,6 +92,8 @@ def _lib():
 def _check(code, what):
     if code != 0:
         msg = _lib().beor_strerror(code).decode()
+        if code in (-2, -3):   # BEOR_ENOMEM, BEOR_ECUDA: name the CUDA error behind it
+            msg += ", " + _lib().beor_last_cuda_error().decode()
         raise BeorError(f"{what}: {msg} ({code})")
 
 

@@ -153,8 +153,11 @@ struct Plan {
   }
 };
 
+thread_local cudaError_t g_last_cuda = cudaSuccess;   // the last CUDA failure seen by this thread
+
 int fail_cuda(beor_ctx* c, cudaError_t e) {
   if (e == cudaSuccess) return BEOR_OK;
+  g_last_cuda = e;
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return BEOR_ENOMEM;
@@ -602,6 +605,8 @@ bool is_mixed(const beor_ctx* c) { return c && c->precision == BEOR_PREC_MIXED; 
 }  // namespace beor
 
 extern "C" {
+
+const char* beor_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda); }
 
 const char* beor_strerror(int code) {
   switch (code) {
