@@ -232,6 +232,9 @@ typedef struct {
                                this is the time lost to the graph's dependencies and launch
                                latencies.  -1 when not measured */
   double ms_busy_main;      /* the same for the launches of the main stream alone */
+  int32_t bounds_error;     /* bounds-checked builds (beor_build_info() & 1): code of the first index
+                               check of the last evaluation that failed (the access was skipped);
+                               0 = none.  Always 0 in the regular build */
 } beor_stats;
 int beor_get_stats(const beor_ctx *ctx, beor_stats *out);
 
@@ -415,6 +418,13 @@ const char *beor_strerror(int code);
 /* Name of the CUDA error behind the calling thread's last BEOR_ECUDA or
  * BEOR_ENOMEM ("cudaSuccess" if none). */
 const char *beor_last_cuda_error(void);
+
+/* Build variant: bit 0 set = the bounds-checked build (compiled with
+ * BEOR_BOUNDS_CHECK), in which the factorisation, solve and residual kernels
+ * check their packed-tile, slice-plane, vector and tensor-map indices,
+ * record the first failure in beor_stats.bounds_error and skip the access
+ * (nothing traps).  The stand-in for a device memory checker. */
+int beor_build_info(void);
 
 #ifdef __cplusplus
 }

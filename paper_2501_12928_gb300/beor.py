@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libbeor.so")
+# BEOR_LIBRARY selects another build of the library (e.g. the bounds-checked
+# _build/libbeor_checked.so); default: the regular build
+LIB_PATH = os.environ.get("BEOR_LIBRARY") or os.path.join(_HERE, "_build", "libbeor.so")
 
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -76,6 +78,8 @@ def _load():
     L.beor_strerror.restype = _c.c_char_p
     L.beor_last_cuda_error.argtypes = []
     L.beor_last_cuda_error.restype = _c.c_char_p
+    L.beor_build_info.argtypes = []
+    L.beor_build_info.restype = _c.c_int
     return L
 
 
@@ -102,7 +106,7 @@ class _Stats(ctypes.Structure):
                 ("ms_last", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("ms_class", ctypes.c_double * 8), ("n_class", ctypes.c_int64 * 8),
                 ("device_error", ctypes.c_int32), ("ms_busy_any", ctypes.c_double),
-                ("ms_busy_main", ctypes.c_double)]
+                ("ms_busy_main", ctypes.c_double), ("bounds_error", ctypes.c_int32)]
 
 
 KERNEL_CLASSES = ("init", "diag", "slice", "panel", "trail", "solve", "refine", "lnl")
@@ -322,6 +326,7 @@ class Likelihood:
         out["device_error"] = st.device_error
         out["ms_busy_any"] = st.ms_busy_any
         out["ms_busy_main"] = st.ms_busy_main
+        out["bounds_error"] = st.bounds_error
         return out
 
     def factor(self, b: int = 0):

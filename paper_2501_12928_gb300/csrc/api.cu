@@ -486,6 +486,8 @@ int build_plan(beor_ctx* const* ctxs, int nsets, const int* Bs, bool need_x, int
   v.rwork = pl->rwork.as<RWork>();
   v.n_rwork = pl->n_rwork;
   v.rows = rows;
+  v.ws_elems = ws_elems;
+  v.dinv_elems = dinv_elems;
   v.grid_rest = pl->sch.rest_ctas;
   v.grid_col = pl->sch.col_ctas;
   if (pl->mixed) {
@@ -607,6 +609,14 @@ bool is_mixed(const beor_ctx* c) { return c && c->precision == BEOR_PREC_MIXED; 
 extern "C" {
 
 const char* beor_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda); }
+
+int beor_build_info(void) {
+#ifdef BEOR_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 const char* beor_strerror(int code) {
   switch (code) {
@@ -848,9 +858,12 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
   if (async && pl->launches > 0 && pl->exec && !first_use) return BEOR_OK;
   CKC(c0, cudaStreamSynchronize(st));
   CKC(c0, cudaGetLastError());
+  int bounds = 0;
   {
-    int err = 0;
-    CKC(c0, cudaMemcpy(&err, &pl->view.flags->error, sizeof(int), cudaMemcpyDeviceToHost));
+    int fl[2] = {0, 0};   // error, bounds
+    CKC(c0, cudaMemcpy(fl, pl->view.flags, sizeof(fl), cudaMemcpyDeviceToHost));
+    const int err = fl[0];
+    bounds = fl[1];
     if (err) {
       for (int s = 0; s < nsets; ++s) {
         ctxs[s]->poisoned = true;
@@ -919,6 +932,7 @@ static int lnl_multi_impl(beor_ctx* const* ctxs, int nsets, const double* const*
     beor_ctx* c = ctxs[s];
     c->stats.ms_last = ms;
     c->stats.device_error = 0;
+    c->stats.bounds_error = bounds;
     c->stats.kernel_launches = pl->launches;
     c->stats.refine_iters_max = pl->mixed && pl->refine_x ? kRefineIters : 0;
     double mx = 0.0;

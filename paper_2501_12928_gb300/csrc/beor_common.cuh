@@ -125,7 +125,25 @@ struct RWork {
 // Bounds of the per-call device state shared by kernels.
 struct Flags {
   int error;              // nonzero: a device-side bounded wait gave up (code)
-  int pad[31];
+  int bounds;             // bounds-checked builds: code of the first index check that failed
+  int pad[30];
+};
+
+// Index checks of the bounds-checked build (-DBEOR_BOUNDS_CHECK), the
+// stand-in for a memory checker: a failed check records its code in the
+// batch's flags (first failure wins) and the access is skipped -- nothing
+// traps.  In the regular build the checks compile away.
+#ifdef BEOR_BOUNDS_CHECK
+#define BEOR_INBOUNDS(flags, cond, code) \
+  ((cond) ? true : (atomicCAS(&(flags)->bounds, 0, (code)), false))
+#else
+#define BEOR_INBOUNDS(flags, cond, code) true
+#endif
+// check codes
+enum {
+  BC_SLICE_ROW = 1, BC_SLICE_OFF = 2, BC_TMA_A = 3, BC_TMA_B = 4, BC_EPI_WS = 5, BC_EPI_EXP = 6,
+  BC_DIAG_WS = 7, BC_DIAG_DINV = 8, BC_DIAG_LINV = 9, BC_SOLVE_VEC = 10, BC_RESID_M = 11, BC_RESID_X = 12,
+  BC_INIT_WS = 13
 };
 
 // Per-problem status values besides 0 (ok), j > 0 (not positive definite at

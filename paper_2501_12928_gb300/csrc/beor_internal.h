@@ -59,6 +59,8 @@ struct BatchView {
   const RWork* rwork;        // CTA work items
   int n_rwork;
   int64_t rows;              // sum of padded dimensions
+  int64_t ws_elems;          // elements of ws (bounds checks)
+  int64_t dinv_elems;        // elements of dinv (bounds checks)
   // bounded waits of the tensor-core kernels: limit of a role's wait on
   // another role (ns), and a test switch (nonzero: the first trailing-update
   // CTA of the evaluation withholds one operand copy, so that the wait on it

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(256) init_ws_f64_kernel(BatchView v) {
   for (int64_t t = blockIdx.y; t < ntiles; t += gridDim.y) {
     int I, J;
     tile_of(t, I, J);
+    if (!BEOR_INBOUNDS(v.flags, pr.ws_off + (t + 1) * BEOR_TILE_ELEMS <= v.ws_elems, BC_INIT_WS)) return;
     const double2* __restrict__ src = sd.M + t * BEOR_TILE_ELEMS;
     double2* __restrict__ dst = reinterpret_cast<double2*>(v.ws) + pr.ws_off + t * BEOR_TILE_ELEMS;
     const double* pinv = v.phi_inv + pr.row_off + (int64_t)I * BEOR_TB;
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(256) init_ws_df_kernel(BatchView v) {
   for (int64_t t = blockIdx.y; t < ntiles; t += gridDim.y) {
     int I, J;
     tile_of(t, I, J);
+    if (!BEOR_INBOUNDS(v.flags, pr.ws_off + (t + 1) * BEOR_TILE_ELEMS <= v.ws_elems, BC_INIT_WS)) return;
     const float4* __restrict__ src = sd.Mdf + t * BEOR_TILE_ELEMS;
     float4* __restrict__ dst = reinterpret_cast<float4*>(v.ws) + pr.ws_off + t * BEOR_TILE_ELEMS;
     for (int e = threadIdx.x; e < BEOR_TILE_ELEMS; e += blockDim.x) dst[e] = src[e];
@@ -179,6 +181,10 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int kg, int mixe
   const int k = kg - pr.k_off;   // this problem's block step
   if (k < 0 || k >= pr.nt) return;
   if (v.status[p] != 0) return;
+  if (!BEOR_INBOUNDS(v.flags, pr.ws_off + (tri_index(k, k) + 1) * BEOR_TILE_ELEMS <= v.ws_elems, BC_DIAG_WS) ||
+      !BEOR_INBOUNDS(v.flags, pr.dinv_off + (int64_t)(k + 1) * DG_PACK <= v.dinv_elems, BC_DIAG_DINV) ||
+      !BEOR_INBOUNDS(v.flags, !mixed || (int64_t)(p + 1) * BEOR_TB <= (int64_t)v.P * BEOR_TB, BC_DIAG_LINV))
+    return;
   WS* ws = reinterpret_cast<WS*>(v.ws) + pr.ws_off + tri_index(k, k) * BEOR_TILE_ELEMS;
   const int tid = threadIdx.x, nthr = blockDim.x;
   for (int e = tid; e < BEOR_TILE_ELEMS; e += nthr) {
@@ -709,6 +715,9 @@ __global__ void __launch_bounds__(256) fwd_step_kernel(BatchView v, int kg, cons
   if (k < -1) return;
   const int i = k + 1 + blockIdx.x;
   if (i >= pr.nt || prob_skipped(v.status[p])) return;
+  if (!BEOR_INBOUNDS(v.flags, pr.row_off + (int64_t)pr.nt * BEOR_TB <= v.rows, BC_SOLVE_VEC) ||
+      !BEOR_INBOUNDS(v.flags, k < 0 || pr.ws_off + (tri_index(i, k) + 1) * BEOR_TILE_ELEMS <= v.ws_elems, BC_SOLVE_VEC))
+    return;
   const int tid = threadIdx.x;
   double2* r = v.vec_t + pr.row_off;
   double2* y = v.vec_y + pr.row_off;
@@ -768,6 +777,7 @@ __global__ void __launch_bounds__(256) bwd_step_kernel(BatchView v, int k, doubl
   const int p = blockIdx.y;
   const Prob pr = v.prob[p];
   if (prob_skipped(v.status[p])) return;
+  if (!BEOR_INBOUNDS(v.flags, pr.row_off + (int64_t)pr.nt * BEOR_TB <= v.rows, BC_SOLVE_VEC)) return;
   const int tid = threadIdx.x;
   double2* r = v.vec_t + pr.row_off;
   double2* x = out + pr.row_off;

@@ -246,6 +246,9 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         const int a_row = (int)(pr.row_off + (int64_t)jb.i * BEOR_TB);
         const int b_row = MODE == MODE_TRAIL ? (int)(pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N)
                                              : jb.p * BEOR_TB + jb.h * MX_N;
+        BEOR_INBOUNDS(v.flags, a_row >= 0 && a_row + MX_M <= v.rows, BC_TMA_A);
+        BEOR_INBOUNDS(v.flags, b_row >= 0 && b_row + MX_N <= (MODE == MODE_TRAIL ? v.rows : (int64_t)v.P * BEOR_TB),
+                      BC_TMA_B);
         if (MODE == MODE_TRAIL) {
           // the epilogue will read this tile's 64 working-matrix columns (128 KB, contiguous)
           const float4* ct = reinterpret_cast<const float4*>(v.ws) + pr.ws_off +
@@ -363,10 +366,18 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       if (lane == 0) mbar_arrive(job_empty(q));
       if (jb.p < 0) break;
       const Prob pr = v.prob[jb.p];
-      const int e_r = pexp[pr.row_off + (int64_t)jb.i * BEOR_TB + r];
+      const int out_j = jb.j;   // trail: block column j; panel: the panel column
+      const bool tile_ok = BEOR_INBOUNDS(
+          v.flags, pr.ws_off + (tri_index(jb.i, out_j) + 1) * BEOR_TILE_ELEMS <= v.ws_elems, BC_EPI_WS);
+      const bool exp_ok = BEOR_INBOUNDS(
+          v.flags,
+          pr.row_off + (int64_t)jb.i * BEOR_TB + r < v.rows &&
+              (MODE == MODE_TRAIL ? pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N + MX_N <= v.rows
+                                  : (int64_t)jb.p * BEOR_TB + jb.h * MX_N + MX_N <= (int64_t)v.P * BEOR_TB),
+          BC_EPI_EXP);
+      const int e_r = exp_ok ? pexp[pr.row_off + (int64_t)jb.i * BEOR_TB + r] : -1000;
       const int32_t* ecol = MODE == MODE_TRAIL ? pexp + pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N
                                                : v.linv_exp + (int64_t)jb.p * BEOR_TB + jb.h * MX_N;
-      const int out_j = jb.j;   // trail: block column j; panel: the panel column
       float4* __restrict__ C = reinterpret_cast<float4*>(v.ws) + pr.ws_off + tri_index(jb.i, out_j) * BEOR_TILE_ELEMS +
                   (int64_t)(jb.h * MX_N) * BEOR_TB + r;
       const uint32_t trow = tmem + ((uint32_t)lane_base << 16);
@@ -374,7 +385,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       constexpr int EC = 4;          // columns per chunk
       // the first working-matrix columns do not depend on the product: load them before it is done
       float4 cv[EC];
-      if (MODE == MODE_TRAIL) {
+      if (MODE == MODE_TRAIL && tile_ok) {
 #pragma unroll
         for (int q = 0; q < EC; ++q) cv[q] = __ldcs(C + (int64_t)(cbeg + q) * BEOR_TB);
       }
@@ -417,7 +428,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       // Phase 2: scale by 2^(e_r + e_c - 14) and subtract from (trail) or
       // store into (panel) the working matrix.
 #pragma unroll
-      for (int c0 = 0; c0 < NC; c0 += EC) {
+      for (int c0 = 0; c0 < NC && tile_ok; c0 += EC) {
         float4 cn[EC];
         if (MODE == MODE_TRAIL && c0 + EC < NC) {
 #pragma unroll
@@ -426,7 +437,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 #pragma unroll
         for (int q = 0; q < EC; ++q) {
           const int c = cbeg + c0 + q;
-          const int ec = __ldg(ecol + c);
+          const int ec = exp_ok ? __ldg(ecol + c) : -1000;
           int ex = e_r + ec - 14;
           if (e_r <= -1000 || ec <= -1000) ex = 0;
           ex = max(-250, min(250, ex));
@@ -473,6 +484,7 @@ __global__ void __launch_bounds__(256)
   const int i = k + 1 + blockIdx.x / (BEOR_TB / R);
   if (k < 0 || i >= pr.nt || prob_skipped(v.status[p])) return;
   const int r0 = (blockIdx.x % (BEOR_TB / R)) * R;
+  if (!BEOR_INBOUNDS(v.flags, pr.ws_off + (tri_index(i, k) + 1) * BEOR_TILE_ELEMS <= v.ws_elems, BC_SLICE_ROW)) return;
   const float4* tile = reinterpret_cast<const float4*>(v.ws) + pr.ws_off + tri_index(i, k) * BEOR_TILE_ELEMS;
   for (int e = threadIdx.x; e < BEOR_TB * R; e += 256) {
     int c = e / R, r = e % R;
@@ -494,7 +506,8 @@ __global__ void __launch_bounds__(256)
     const int e = mx > 0.0f ? ilogbf(mx) + 1 : -1000;
     if (lane == 0) {
       s_e[r] = e;
-      panel_exp[pr.row_off + (int64_t)i * BEOR_TB + r0 + r] = e;
+      if (BEOR_INBOUNDS(v.flags, pr.row_off + (int64_t)i * BEOR_TB + r0 + r < rows, BC_SLICE_ROW))
+        panel_exp[pr.row_off + (int64_t)i * BEOR_TB + r0 + r] = e;
     }
   }
   __syncthreads();
@@ -547,6 +560,7 @@ __global__ void __launch_bounds__(256)
     }
   }
   const int64_t off = slice_elem_off(grow, c0, rows);   // a multiple of 8 elements: 16-byte aligned
+  if (!BEOR_INBOUNDS(v.flags, grow < rows && off + 8 <= rows * BEOR_TB, BC_SLICE_OFF)) return;
 #pragma unroll
   for (int pl = 0; pl < BEOR_NPLANE; ++pl)
     *reinterpret_cast<uint4*>(panel_sl + (int64_t)pl * rows * BEOR_TB + off) =
@@ -793,6 +807,10 @@ __global__ void __launch_bounds__(256, 2) resid_df_kernel(BatchView v) {
   double tre[8], tim[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) tre[q] = tim[q] = 0.0;
+  if (!BEOR_INBOUNDS(v.flags, w.I >= 0 && w.I < sd.nt && w.j0 >= 0 && w.j1 <= sd.nt, BC_RESID_M)) return;
+  if (threadIdx.x < RG && roff[threadIdx.x] >= 0 &&
+      !BEOR_INBOUNDS(v.flags, roff[threadIdx.x] + (int64_t)sd.nt * BEOR_TB <= v.rows, BC_RESID_X))
+    roff[threadIdx.x] = -1;
   for (int J = w.j0; J < w.j1; ++J) {
     __syncthreads();
     for (int e = threadIdx.x; e < RG * BEOR_TB * 6; e += blockDim.x) {
