@@ -168,8 +168,9 @@ struct HkJob {
 
 // M tile (i, j) columns h*64.. += conj(sum over the pass's K-blocks), or =
 // when `accumulate` is 0.  Tiles from `counter` (zeroed before the launch).
-// 576 threads x 112 registers fit the SM's 65,536
-__global__ void __maxnreg__(112)
+// 576 threads: 18 warps over the SM's four register-file partitions (16,384
+// registers each), five warps on some: at most 96 registers per thread
+__global__ void __launch_bounds__(HK_THREADS, 1)
     herk_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                    const int32_t* __restrict__ exps, int64_t rows, int nt, int nkb, int accumulate,
                    double2* __restrict__ Mt, int* __restrict__ counter, int* __restrict__ err) {
