@@ -12,7 +12,7 @@ term) rounds once per product it receives, about 320 times per K-block, and
 the roundings add up almost linearly: up to about 2^-48 x 320 ~ 2^-40 of
 the largest element per block.  The bound 2^-38 of max |M| is below
 float64 accumulation's own worst case over these K (K 2^-53, 1e-11 at
-90,972 visibilities); lnL parity is the criterion that matters.
+90,972 visibilities); lnL parity is the criterion that matters."""
 
 import time
 
