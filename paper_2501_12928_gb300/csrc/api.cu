@@ -249,7 +249,7 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
     }
     for (int k = 0; k + 1 < pl.max_nt; ++k) {
       RUN(KC_TRAIL, launch_trail_mixed(v, pl.maps, k, TRAIL_NEXT_COL, s, hi));
-      L += 1;
+      L += trail_launch_count(pl.maps, k, TRAIL_NEXT_COL);
       if ((e = cudaEventRecord(pl.ev_col, s)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(pl.side, pl.ev_col, 0)) != cudaSuccess) return e;
       RUN(KC_DIAG, launch_diag(v, k + 1, true, s, hi));
@@ -270,7 +270,7 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
           cap = std::max(8, device_sms() - active);
         }
         RUN_ON(KC_TRAIL, pl.side, launch_trail_mixed(v, pl.maps, k, TRAIL_REST, pl.side, 0, cap));
-        L += 1;
+        L += trail_launch_count(pl.maps, k, TRAIL_REST);
       }
       if ((e = cudaEventRecord(pl.ev_rest, pl.side)) != cudaSuccess) return e;
       if (k + 2 < pl.max_nt) {
@@ -293,7 +293,7 @@ cudaError_t run_sequence(Plan& pl, cudaStream_t s, int64_t* nlaunch, bool mark) 
           RUN(KC_PANEL, launch_panel_mixed(v, pl.maps, k, s));
           RUN(KC_SLICE, launch_slice_panel(v, k, s));
           RUN(KC_TRAIL, launch_trail_mixed(v, pl.maps, k, TRAIL_ALL, s));
-          L += 4;
+          L += 3 + trail_launch_count(pl.maps, k, TRAIL_ALL);
         } else {
           RUN(KC_PANEL, launch_panel_f64(v, k, s));
           RUN(KC_TRAIL, launch_trail_f64(v, k, s));

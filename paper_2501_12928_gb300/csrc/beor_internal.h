@@ -118,9 +118,12 @@ cudaError_t mixed_reset_counters(const MixedMaps* m, cudaStream_t s);   // befor
 int64_t mixed_tiles(const MixedMaps* m, int kind, int k);               // kind 0 next col, 1 rest, 2 panel, 3 all
 cudaError_t launch_slice_panel(const BatchView& v, int k, cudaStream_t s, int prio = 0);
 cudaError_t launch_panel_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s, int prio = 0);
-// max_ctas > 0 caps the launch's CTAs further (below the schedule's cap)
+// The trailing update is two launches: its off-diagonal tiles (reduced slice
+// pair set) and its diagonal tiles (full set).  max_ctas > 0 caps each
+// launch's CTAs further (below the schedule's cap).
 cudaError_t launch_trail_mixed(const BatchView& v, const MixedMaps* m, int k, int part, cudaStream_t s,
                                int prio = 0, int max_ctas = 0);
+int trail_launch_count(const MixedMaps* m, int k, int part);   // kernels launch_trail_mixed launches
 int device_sms();   // SMs of the current device
 cudaError_t launch_residual(const BatchView& v, cudaStream_t s);      // vec_r = dbar - Sigma x (float64)
 cudaError_t launch_refine_update(const BatchView& v, cudaStream_t s); // x += vec_d; residual norm

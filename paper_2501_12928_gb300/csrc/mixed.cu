@@ -30,9 +30,12 @@
 // 18 with separate re / im accumulators, which cuts the tensor cores' reads
 // of A from shared memory by 40 %.  The slice planes hold the parts
 // (Im, Re, -Im) of each slice for that reason.  Warp 0 issues TMA loads into
-// a 5-slot shared-memory ring of half-stages (one A part of 128 rows and its
-// B window of 64 rows, every slice, one K-chunk of 16: 40 KB), fetched from
-// the planes stored in the tensor cores' no-swizzle order as 512-byte rows;
+// a shared-memory ring of half-stages (one A part of 128 rows and its B
+// window of 64 rows, one K-chunk of 16), fetched from the planes stored in
+// the tensor cores' no-swizzle order as 512-byte rows: slices 0..3 in slots
+// of 32 KB (7 of them) for the trailing update's off-diagonal tiles, all five
+// slices in slots of 40 KB (5 of them) for its diagonal tiles and the panel
+// product;
 // warp 1 issues the tcgen05.mma instructions (M = 128, N = 128 or 256,
 // K = 16, bf16 -> fp32); warps 2-9 (two per TMEM lane quarter, each with half
 // the columns) drain TMEM and apply the update.  Every wait is bounded by a
@@ -54,21 +57,37 @@ namespace beor {
 constexpr int MX_M = 128;                // output rows per tile
 constexpr int MX_N = 64;                 // output complex columns per tile
 constexpr int MX_KC = 16;                // complex K per pipeline stage
-constexpr int MX_SLOTS = 5;              // half-stage ring (two half-stages per K-chunk)
-constexpr int MX_A_BYTES = BEOR_NSLICE * MX_M * MX_KC * 2;       // 20480: one A part, every slice
-constexpr int MX_B_BYTES = BEOR_NSLICE * 2 * MX_N * MX_KC * 2;   // 20480: a two-part B window, every slice
-constexpr int MX_HALF_BYTES = MX_A_BYTES + MX_B_BYTES;            // 40960
 constexpr int MX_SLICE_A = MX_M * MX_KC * 2;                      // 4096: one slice of the A part
 constexpr int MX_SLICE_B = 2 * MX_N * MX_KC * 2;                  // 4096: one slice of the B window
-constexpr int MX_SMEM = MX_SLOTS * MX_HALF_BYTES + 1024 + 256;   // 206080
+// Kernel modes: the trailing update's off-diagonal tiles (reduced pair set,
+// slices 0..3), its diagonal tiles (full set) and the panel product (full
+// set).  The diagonal tiles have a launch of their own so that the
+// off-diagonal kernel, which does nearly all the work, carries no second
+// product schedule: with one in the same loop its tensor-core products
+// issued about a fifth slower.
+enum { MODE_TRAIL = 0, MODE_PANEL = 1, MODE_TRAIL_DIAG = 2 };
+// Operand ring per mode: slots of one half-stage (A part, then its B
+// window), slices 0..3 (32 KB, 7 slots) for the reduced set, all five
+// slices (40 KB, 5 slots) for the full one.
+template <int MODE>
+struct Ring {
+  static constexpr int nslice = MODE == MODE_TRAIL ? 4 : BEOR_NSLICE;
+  static constexpr int a_bytes = nslice * MX_SLICE_A;
+  static constexpr int slot = nslice * (MX_SLICE_A + MX_SLICE_B);
+  static constexpr int slots = MODE == MODE_TRAIL ? 7 : 5;
+  static constexpr int smem = slots * slot + 1024 + 320;   // 230720 (reduced set), 206144 (full set)
+  static constexpr int set = MODE == MODE_TRAIL ? SLICE_PAIRS_REDUCED : SLICE_PAIRS_FULL5;
+};
 constexpr int MX_EPI_WARPS = 8;        // two warps per TMEM lane quarter, each draining half the columns
 constexpr int MX_THREADS = 64 + 32 * MX_EPI_WARPS;
 constexpr uint32_t MX_TMEM_COLS = 512;
 constexpr unsigned long long MX_TIMEOUT_NS = TC_DRAIN_NS;   // default role-wait limit
 
-enum { MODE_TRAIL = 0, MODE_PANEL = 1 };
-// trailing tiles of block step k: the next block column (j = k + 1) or the rest (j >= k + 2)
-enum { KIND_COL = 0, KIND_REST = 1, KIND_PANEL = 2, KIND_ALL = 3 };
+// Tiles of block step k.  Trailing update: the next block column (j = k + 1),
+// the rest (j >= k + 2), or all (j >= k + 1), each as its off-diagonal tiles
+// (i > j) and its diagonal tiles (i = j); panel product: i >= k + 1, j = k.
+enum { KIND_COL = 0, KIND_REST = 1, KIND_PANEL = 2, KIND_ALL = 3, KIND_DCOL = 4, KIND_DREST = 5, KIND_DALL = 6,
+       KIND_COUNT = 7 };
 constexpr int MX_JOBS = 4;               // depth of the producer -> MMA / epilogue job ring
 enum { ERR_TMA_WAIT = 11, ERR_MMA_WAIT = 12, ERR_ACC_WAIT = 13, ERR_EPI_WAIT = 14 };
 
@@ -78,10 +97,10 @@ struct MixedMaps {
   CUtensorMap linv_b;       // inverse-diagonal slices, box 64 rows x 2 parts
   CUtensorMap panel_a4[2];  // as panel_a / panel_b, slices 0..3 only (off-diagonal trailing tiles)
   CUtensorMap panel_b4[2];
-  int64_t* d_prefix = nullptr;   // [4][max_nt][P+1] tile prefix sums (kinds col, rest, panel, all)
-  int* d_counter = nullptr;      // [4][max_nt] dynamic tile counters, zeroed before every evaluation
+  int64_t* d_prefix = nullptr;   // [KIND_COUNT][max_nt][P+1] tile prefix sums
+  int* d_counter = nullptr;      // [KIND_COUNT][max_nt] dynamic tile counters, zeroed before every evaluation
   int max_nt = 0, P = 0;
-  std::vector<int64_t> h_total[4];
+  std::vector<int64_t> h_total[KIND_COUNT];
 };
 
 // ---------------------------------------------------------------------------
@@ -114,15 +133,21 @@ __device__ __forceinline__ bool decode_tile(const BatchView& v, const int64_t* p
   jb.p = p;
   jb.h = (int)(u % (BEOR_TB / MX_N));
   u /= (BEOR_TB / MX_N);
-  if (kind == KIND_REST || kind == KIND_ALL) {
+  if (kind == KIND_REST || kind == KIND_ALL) {   // i > j >= j0
     const int j0 = kind == KIND_REST ? k + 2 : k + 1;
     int a, b;
     tri_pair(u, a, b);
-    jb.i = j0 + a;
+    jb.i = j0 + a + 1;
     jb.j = j0 + b;
-  } else {
+  } else if (kind == KIND_COL) {                 // i >= k + 2, j = k + 1
+    jb.i = k + 2 + (int)u;
+    jb.j = k + 1;
+  } else if (kind == KIND_PANEL) {               // i >= k + 1, j = k
     jb.i = k + 1 + (int)u;
-    jb.j = kind == KIND_COL ? k + 1 : k;
+    jb.j = k;
+  } else {                                       // diagonal: i = j >= j0
+    const int j0 = kind == KIND_DREST ? k + 2 : k + 1;
+    jb.i = jb.j = j0 + (int)u;
   }
   return jb.i < v.prob[p].nt;
 }
@@ -131,50 +156,51 @@ __device__ __forceinline__ bool decode_tile(const BatchView& v, const int64_t* p
 // the slice GEMM
 // ---------------------------------------------------------------------------
 // Products of one half-stage: every A slice with its B window (schedule
-// slice_mma_*, full or reduced pair set).  The first two products of a tile
-// (K-chunk 0, part Im, slice 0) cover all 512 columns and overwrite them.
+// slice_mma_*, full or reduced pair set); ad, bd describe slice 0 of the A
+// part and of the B window.  The first two products of a tile (K-chunk 0,
+// part Im, slice 0) cover all 512 columns and overwrite them.
 template <int SET>
-__device__ __forceinline__ void issue_half_stage(uint32_t tmem, uint32_t a0, uint32_t b0, bool first) {
+__device__ __forceinline__ void issue_half_stage(uint32_t tmem, uint64_t ad, uint64_t bd, bool first) {
 #pragma unroll
   for (int sa = 0; sa < BEOR_NSLICE; ++sa) {
-    const uint64_t ad = sdesc_kmajor(a0 + sa * MX_SLICE_A);
 #pragma unroll
     for (int q = 0; q < slice_mma_count(sa, SET); ++q) {
       const uint32_t acc = (first && sa == 0 && q < slice_mma_main(0)) ? 0u : 1u;
-      tc_mma(tmem + (uint32_t)slice_mma_col(sa, q), ad,
-             sdesc_kmajor(b0 + slice_mma_t(sa, q, SET) * MX_SLICE_B), idesc_bf16(0, (uint32_t)slice_mma_n(sa, q)),
-             acc);
+      tc_mma(tmem + (uint32_t)slice_mma_col(sa, q), sdesc_add(ad, sa * MX_SLICE_A),
+             sdesc_add(bd, slice_mma_t(sa, q, SET) * MX_SLICE_B), idesc_bf16(0, (uint32_t)slice_mma_n(sa, q)), acc);
     }
   }
 }
 
-// map_a / map_b: boxes of all 5 slices; map_a4 / map_b4: of slices 0..3, for
-// the trailing update's off-diagonal tiles (reduced pair set).
+// map_a / map_b: the A and B boxes of one half-stage (Ring<MODE>::nslice
+// slices).
 template <int MODE>
 __global__ void __launch_bounds__(MX_THREADS, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-                      const __grid_constant__ CUtensorMap map_a4, const __grid_constant__ CUtensorMap map_b4,
                       BatchView v, const int64_t* __restrict__ prefix, int64_t ntiles, int k, int kind,
                       int* __restrict__ counter, const int32_t* __restrict__ pexp) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + MX_SLOTS * MX_HALF_BYTES);
-  // bars[0..4] full, [5..9] empty, [10] acc_full, [11] acc_empty, [12] drain,
-  // [13..16] job_full, [17..20] job_empty; then the TMEM address, the abort
-  // flag and the job ring (256 bytes in all)
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 21);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 22);
-  TileJob* jobs = reinterpret_cast<TileJob*>(bars + 24);   // MX_JOBS slots
-  static_assert(24 * 8 + MX_JOBS * sizeof(TileJob) <= 256, "barrier area");
+  constexpr int SLOTS = Ring<MODE>::slots, SLOT = Ring<MODE>::slot, ABYTES = Ring<MODE>::a_bytes;
+  constexpr bool TRAILING = MODE != MODE_PANEL;   // subtract from the working matrix (else store)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SLOTS * SLOT);
+  // bars [0, SLOTS) full, [SLOTS, 2 SLOTS) empty, then acc_full, acc_empty,
+  // drain, job_full[MX_JOBS], job_empty[MX_JOBS]; then the TMEM address, the
+  // abort flag and the job ring (320 bytes in all)
+  constexpr int NB = 2 * SLOTS + 3 + 2 * MX_JOBS;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + NB);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + NB + 1);
+  TileJob* jobs = reinterpret_cast<TileJob*>(bars + NB + 2);   // MX_JOBS slots
+  static_assert((NB + 2) * 8 + MX_JOBS * sizeof(TileJob) <= 320, "barrier area");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long wait_ns = v.wait_ns ? v.wait_ns : MX_TIMEOUT_NS;
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
-  auto empty_bar = [&](int s) { return bar0 + 8u * (MX_SLOTS + s); };
-  const uint32_t acc_full = bar0 + 8u * 10, acc_empty = bar0 + 8u * 11, drain = bar0 + 8u * 12;
-  auto job_full = [&](uint32_t q) { return bar0 + 8u * (13 + q); };
-  auto job_empty = [&](uint32_t q) { return bar0 + 8u * (17 + q); };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (SLOTS + s); };
+  const uint32_t acc_full = bar0 + 8u * (2 * SLOTS), acc_empty = acc_full + 8u, drain = acc_full + 16u;
+  auto job_full = [&](uint32_t q) { return bar0 + 8u * (2 * SLOTS + 3 + q); };
+  auto job_empty = [&](uint32_t q) { return bar0 + 8u * (2 * SLOTS + 3 + MX_JOBS + q); };
 
   // After a bounded wait gave up anywhere in this evaluation, the remaining
   // launches return at once (read by one thread, so the whole CTA agrees)
@@ -187,7 +213,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   }
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < MX_SLOTS; ++s) {
+    for (int s = 0; s < SLOTS; ++s) {
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
@@ -202,10 +228,6 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     prefetch_map(&map_a);
     prefetch_map(&map_b);
-    if (MODE == MODE_TRAIL) {
-      prefetch_map(&map_a4);
-      prefetch_map(&map_b4);
-    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
@@ -223,8 +245,9 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     // a concurrent kernel released their SM, simply take fewer) and published
     // to the MMA and epilogue warps through a ring of MX_JOBS slots.
     if (lane == 0) {
-      uint32_t it = 0;
-      uint32_t withheld = ~0u;   // iteration whose copy the test switch withheld (never waited for)
+      uint32_t it = 0;           // half-stages issued
+      uint32_t ps = 0, pph = 0;  // ring slot and phase of half-stage it
+      uint32_t withheld = ~0u;   // half-stage whose copy the test switch withheld (never waited for)
       for (uint32_t n = 0;; ++n) {
         const uint32_t q = n % MX_JOBS;
         if (!mbar_wait(job_empty(q), ((n / MX_JOBS) & 1) ^ 1, abort_flag, wait_ns)) {
@@ -244,12 +267,12 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         if (jb.p < 0) break;
         const Prob pr = v.prob[jb.p];
         const int a_row = (int)(pr.row_off + (int64_t)jb.i * BEOR_TB);
-        const int b_row = MODE == MODE_TRAIL ? (int)(pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N)
-                                             : jb.p * BEOR_TB + jb.h * MX_N;
+        const int b_row = TRAILING ? (int)(pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N)
+                                   : jb.p * BEOR_TB + jb.h * MX_N;
         BEOR_INBOUNDS(v.flags, a_row >= 0 && a_row + MX_M <= v.rows, BC_TMA_A);
-        BEOR_INBOUNDS(v.flags, b_row >= 0 && b_row + MX_N <= (MODE == MODE_TRAIL ? v.rows : (int64_t)v.P * BEOR_TB),
+        BEOR_INBOUNDS(v.flags, b_row >= 0 && b_row + MX_N <= (TRAILING ? v.rows : (int64_t)v.P * BEOR_TB),
                       BC_TMA_B);
-        if (MODE == MODE_TRAIL) {
+        if (TRAILING) {
           // the epilogue will read this tile's 64 working-matrix columns (128 KB, contiguous)
           const float4* ct = reinterpret_cast<const float4*>(v.ws) + pr.ws_off +
                              tri_index(jb.i, jb.j) * BEOR_TILE_ELEMS + (int64_t)(jb.h * MX_N) * BEOR_TB;
@@ -259,44 +282,45 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         // (Im, Re), h = 1 A part Re with the window (Re, -Im)
         for (int kc = 0; kc < BEOR_TB / MX_KC; ++kc) {
           for (int h = 0; h < 2; ++h, ++it) {
-            const int s = it % MX_SLOTS;
-            const uint32_t ph = (it / MX_SLOTS) & 1;
-            if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag, wait_ns)) {
+            if (!mbar_wait(empty_bar(ps), pph ^ 1, abort_flag, wait_ns)) {
               atomicCAS(&v.flags->error, 0, ERR_TMA_WAIT);
               *abort_flag = 1;
               goto producer_done;
             }
-            if (MODE == MODE_TRAIL && v.test_skip_copy && blockIdx.x == 0 && n == 0 && kc == 3 && h == 0) {
-              // test switch: no copy and no arrival for this half-stage, so
-              // the MMA warp's wait on it can only end by its limit
+            const uint32_t s = ps;
+            if (++ps == SLOTS) {
+              ps = 0;
+              pph ^= 1;
+            }
+            if (TRAILING && v.test_skip_copy && blockIdx.x == 0 && n == 0 && kc == 3 && h == 0) {
+              // test switch: no copy and no arrival for this slot, so the
+              // MMA warp's wait on it can only end by its limit (the first
+              // CTA of each trailing launch; once one wait has given up, the
+              // later launches return at once)
               withheld = it;
               continue;
             }
-            const uint32_t dst = sbase + s * MX_HALF_BYTES;
-            // x = 0 always (16-byte aligned); y counts pairs of 8-row groups.
-            // Off-diagonal trailing tiles never read slice 4 (reduced pair
-            // set): four-slice boxes, placed where the five-slice ones are.
-            if (MODE == MODE_TRAIL && jb.i != jb.j) {
-              mbar_expect_tx(full_bar(s), MX_HALF_BYTES * 4 / 5);
-              tma_load_5d(dst, &map_a4, 0, a_row / 16, kc, h, 0, full_bar(s));
-              tma_load_5d(dst + MX_A_BYTES, &map_b4, 0, b_row / 16, kc, h, 0, full_bar(s));
-            } else {
-              mbar_expect_tx(full_bar(s), MX_HALF_BYTES);
-              tma_load_5d(dst, &map_a, 0, a_row / 16, kc, h, 0, full_bar(s));
-              tma_load_5d(dst + MX_A_BYTES, &map_b, 0, b_row / 16, kc, h, 0, full_bar(s));
-            }
+            const uint32_t dst = sbase + s * SLOT;
+            // x = 0 always (16-byte aligned); y counts pairs of 8-row groups
+            mbar_expect_tx(full_bar(s), SLOT);
+            tma_load_5d(dst, &map_a, 0, a_row / 16, kc, h, 0, full_bar(s));
+            tma_load_5d(dst + ABYTES, &map_b, 0, b_row / 16, kc, h, 0, full_bar(s));
           }
         }
       }
     producer_done:
       // drain: every issued copy must have landed before the CTA may exit
-      for (uint32_t q = (it >= MX_SLOTS ? it - MX_SLOTS : 0); q < it; ++q)
-        if (q != withheld) mbar_wait_deadline(full_bar(q % MX_SLOTS), (q / MX_SLOTS) & 1);
+      for (uint32_t q = (it >= SLOTS ? it - SLOTS : 0); q < it; ++q)
+        if (q != withheld) mbar_wait_deadline(full_bar(q % SLOTS), (q / SLOTS) & 1);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      uint32_t it = 0, tcount = 0;
+      // ring position (slot rs, phase rph), advanced slot by slot without
+      // divisions: the thread issues back to back and must not leave gaps
+      // in the tensor pipe between half-stages
+      uint32_t rs = 0, rph = 0, tcount = 0;
+      const uint64_t desc0 = sdesc_kmajor(sbase);
       for (uint32_t n = 0;; ++n) {
         const uint32_t q = n % MX_JOBS;
         if (!mbar_wait(job_full(q), (n / MX_JOBS) & 1, abort_flag, wait_ns)) {
@@ -315,29 +339,25 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         tc_fence_after();
         bool bad = false;
         for (int kc = 0; kc < BEOR_TB / MX_KC && !bad; ++kc) {
-          for (int h = 0; h < 2; ++h, ++it) {
-            const int s = it % MX_SLOTS;
-            const uint32_t ph = (it / MX_SLOTS) & 1;
-            if (!mbar_wait(full_bar(s), ph, abort_flag, wait_ns)) {
+          for (int h = 0; h < 2; ++h) {
+            if (!mbar_wait(full_bar(rs), rph, abort_flag, wait_ns)) {
               atomicCAS(&v.flags->error, 0, ERR_MMA_WAIT);
               *abort_flag = 1;
               bad = true;
               break;
             }
             tc_fence_after();
-            const uint32_t a0 = sbase + s * MX_HALF_BYTES, b0 = a0 + MX_A_BYTES;
+            const uint64_t ad = sdesc_add(desc0, rs * SLOT), bd = sdesc_add(ad, ABYTES);
             // A slice sa times B slices t contributes to level min(sa + t, 3)
             // (schedule: slice_mma_*); the window's slices lie at 4 KB steps in
             // shared memory, their two parts 64 rows apart, so that a product
-            // over two levels reads 256 consecutive rows.  The panel product
-            // and the diagonal tiles of the trailing update take the full pair
-            // set, the other trailing tiles the reduced one.
-            const bool first = kc == 0 && h == 0;
-            if (MODE == MODE_PANEL || jb.i == jb.j)
-              issue_half_stage<SLICE_PAIRS_FULL5>(tmem, a0, b0, first);
-            else
-              issue_half_stage<SLICE_PAIRS_REDUCED>(tmem, a0, b0, first);
-            tc_commit(empty_bar(s));
+            // over two levels reads 256 consecutive rows
+            issue_half_stage<Ring<MODE>::set>(tmem, ad, bd, kc == 0 && h == 0);
+            tc_commit(empty_bar(rs));
+            if (++rs == SLOTS) {
+              rs = 0;
+              rph ^= 1;
+            }
           }
         }
         if (bad) break;
@@ -372,11 +392,11 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       const bool exp_ok = BEOR_INBOUNDS(
           v.flags,
           pr.row_off + (int64_t)jb.i * BEOR_TB + r < v.rows &&
-              (MODE == MODE_TRAIL ? pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N + MX_N <= v.rows
+              (TRAILING ? pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N + MX_N <= v.rows
                                   : (int64_t)jb.p * BEOR_TB + jb.h * MX_N + MX_N <= (int64_t)v.P * BEOR_TB),
           BC_EPI_EXP);
       const int e_r = exp_ok ? pexp[pr.row_off + (int64_t)jb.i * BEOR_TB + r] : -1000;
-      const int32_t* ecol = MODE == MODE_TRAIL ? pexp + pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N
+      const int32_t* ecol = TRAILING ? pexp + pr.row_off + (int64_t)jb.j * BEOR_TB + jb.h * MX_N
                                                : v.linv_exp + (int64_t)jb.p * BEOR_TB + jb.h * MX_N;
       float4* __restrict__ C = reinterpret_cast<float4*>(v.ws) + pr.ws_off + tri_index(jb.i, out_j) * BEOR_TILE_ELEMS +
                   (int64_t)(jb.h * MX_N) * BEOR_TB + r;
@@ -385,7 +405,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       constexpr int EC = 4;          // columns per chunk
       // the first working-matrix columns do not depend on the product: load them before it is done
       float4 cv[EC];
-      if (MODE == MODE_TRAIL && tile_ok) {
+      if (TRAILING && tile_ok) {
 #pragma unroll
         for (int q = 0; q < EC; ++q) cv[q] = __ldcs(C + (int64_t)(cbeg + q) * BEOR_TB);
       }
@@ -430,7 +450,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 #pragma unroll
       for (int c0 = 0; c0 < NC && tile_ok; c0 += EC) {
         float4 cn[EC];
-        if (MODE == MODE_TRAIL && c0 + EC < NC) {
+        if (TRAILING && c0 + EC < NC) {
 #pragma unroll
           for (int q = 0; q < EC; ++q) cn[q] = __ldcs(C + (int64_t)(cbeg + c0 + EC + q) * BEOR_TB);
         }
@@ -446,7 +466,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           const dfl vr{prh[c0 + q] * s1 * s2, prl[c0 + q] * s1 * s2};
           const dfl vi{pih[c0 + q] * s1 * s2, pil[c0 + q] * s1 * s2};
           float4* cp = C + (int64_t)c * BEOR_TB;
-          if (MODE == MODE_TRAIL) {
+          if (TRAILING) {
             const float4 w = cv[q];
             const dfl wr = df_sub_quick(dfl{w.x, w.y}, vr);
             const dfl wi = df_sub_quick(dfl{w.z, w.w}, vi);
@@ -455,7 +475,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
             __stcs(cp, make_float4(vr.hi, vr.lo, vi.hi, vi.lo));
           }
         }
-        if (MODE == MODE_TRAIL) {
+        if (TRAILING) {
 #pragma unroll
           for (int q = 0; q < EC; ++q) cv[q] = cn[q];
         }
@@ -643,33 +663,43 @@ cudaError_t mixed_maps_create(const BatchView& v, MixedMaps** out) {
   m->max_nt = v.max_nt;
   m->P = v.P;
   const int H = BEOR_TB / MX_N;
-  std::vector<int64_t> pre((size_t)4 * v.max_nt * (v.P + 1), 0);
-  for (int kind = 0; kind < 4; ++kind) m->h_total[kind].assign(v.max_nt, 0);
-  for (int kind = 0; kind < 4; ++kind)
+  std::vector<int64_t> pre((size_t)KIND_COUNT * v.max_nt * (v.P + 1), 0);
+  for (int kind = 0; kind < KIND_COUNT; ++kind) m->h_total[kind].assign(v.max_nt, 0);
+  for (int kind = 0; kind < KIND_COUNT; ++kind)
     for (int k = 0; k < v.max_nt; ++k) {
       int64_t* pk = pre.data() + ((size_t)kind * v.max_nt + k) * (v.P + 1);
       for (int p = 0; p < v.P; ++p) {
         const int kp = k - hp[p].k_off;                      // the problem's own block step
-        const int64_t T = kp < 0 ? 0 : std::max(0, hp[p].nt - kp - 1);   // block rows below the diagonal
+        const int T = kp < 0 ? 0 : std::max(0, hp[p].nt - kp - 1);   // block rows below the diagonal
         int64_t n = 0;
-        if (kind == KIND_COL || kind == KIND_PANEL) n = T;
-        else if (kind == KIND_REST) n = tri_count((int)std::max<int64_t>(0, T - 1));
-        else n = tri_count((int)T);
+        switch (kind) {
+          case KIND_PANEL: n = T; break;                          // i >= k + 1
+          case KIND_COL: n = std::max(0, T - 1); break;           // i >= k + 2, j = k + 1
+          case KIND_DCOL: n = T > 0 ? 1 : 0; break;               // (k + 1, k + 1)
+          case KIND_REST: n = tri_count(std::max(0, T - 2)); break;   // i > j >= k + 2
+          case KIND_DREST: n = std::max(0, T - 1); break;         // i = j >= k + 2
+          case KIND_ALL: n = tri_count(std::max(0, T - 1)); break;    // i > j >= k + 1
+          default: n = T; break;                                  // KIND_DALL: i = j >= k + 1
+        }
         pk[p + 1] = pk[p] + n * H;
       }
       m->h_total[kind][k] = pk[v.P];
     }
   e = cudaMalloc(&m->d_prefix, sizeof(int64_t) * pre.size());
   if (e == cudaSuccess) e = cudaMemcpy(m->d_prefix, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&m->d_counter, sizeof(int) * 4 * (size_t)v.max_nt);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_counter, sizeof(int) * KIND_COUNT * (size_t)v.max_nt);
   if (e != cudaSuccess) {
     mixed_maps_destroy(m);
     return e;
   }
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(slice_gemm_kernel<MODE_TRAIL>, cudaFuncAttributeMaxDynamicSharedMemorySize, MX_SMEM);
-    cudaFuncSetAttribute(slice_gemm_kernel<MODE_PANEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, MX_SMEM);
+    cudaFuncSetAttribute(slice_gemm_kernel<MODE_TRAIL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Ring<MODE_TRAIL>::smem);
+    cudaFuncSetAttribute(slice_gemm_kernel<MODE_TRAIL_DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Ring<MODE_TRAIL_DIAG>::smem);
+    cudaFuncSetAttribute(slice_gemm_kernel<MODE_PANEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Ring<MODE_PANEL>::smem);
     attr = true;
   }
   *out = m;
@@ -684,11 +714,17 @@ void mixed_maps_destroy(MixedMaps* m) {
 }
 
 cudaError_t mixed_reset_counters(const MixedMaps* m, cudaStream_t s) {
-  return cudaMemsetAsync(m->d_counter, 0, sizeof(int) * 4 * (size_t)m->max_nt, s);
+  return cudaMemsetAsync(m->d_counter, 0, sizeof(int) * KIND_COUNT * (size_t)m->max_nt, s);
+}
+
+static int64_t mixed_tiles_kind(const MixedMaps* m, int kind, int k) {
+  return k >= 0 && k < m->max_nt ? m->h_total[kind][k] : 0;
 }
 
 int64_t mixed_tiles(const MixedMaps* m, int kind, int k) {
-  return k >= 0 && k < m->max_nt ? m->h_total[kind][k] : 0;
+  if (k < 0 || k >= m->max_nt) return 0;
+  const int diag = kind == KIND_COL ? KIND_DCOL : kind == KIND_REST ? KIND_DREST : kind == KIND_ALL ? KIND_DALL : -1;
+  return m->h_total[kind][k] + (diag >= 0 ? m->h_total[diag][k] : 0);
 }
 
 static int num_sms() {
@@ -706,29 +742,44 @@ static cudaError_t launch_gemm(const BatchView& v, const MixedMaps* m, int k, in
                                int max_ctas = 0) {
   const int64_t nt = m->h_total[kind][k];
   if (nt <= 0) return cudaSuccess;
-  int cap = kind == KIND_REST ? v.grid_rest : (kind == KIND_COL || kind == KIND_PANEL) ? v.grid_col : 0;
+  int cap = (kind == KIND_REST || kind == KIND_DREST) ? v.grid_rest
+            : (kind == KIND_COL || kind == KIND_DCOL || kind == KIND_PANEL) ? v.grid_col : 0;
   if (cap <= 0) cap = num_sms();
   if (max_ctas > 0) cap = std::min(cap, max_ctas);
   const int grid = (int)std::min<int64_t>(nt, cap);
   const int64_t* pre = m->d_prefix + ((size_t)kind * m->max_nt + k) * (m->P + 1);
   int* ctr = m->d_counter + (size_t)kind * m->max_nt + k;
+  const int32_t* pexp = (const int32_t*)exp_buf(v, k);
   if (kind == KIND_PANEL)
-    return launch_prio(slice_gemm_kernel<MODE_PANEL>, dim3(grid), dim3(MX_THREADS), (size_t)MX_SMEM, s, prio,
-                       m->panel_a[k & 1], m->linv_b, m->panel_a[k & 1], m->linv_b, v, pre, nt, k, kind, ctr,
-                       (const int32_t*)exp_buf(v, k));
-  return launch_prio(slice_gemm_kernel<MODE_TRAIL>, dim3(grid), dim3(MX_THREADS), (size_t)MX_SMEM, s, prio,
-                     m->panel_a[k & 1], m->panel_b[k & 1], m->panel_a4[k & 1], m->panel_b4[k & 1], v, pre, nt, k,
-                     kind, ctr, (const int32_t*)exp_buf(v, k));
+    return launch_prio(slice_gemm_kernel<MODE_PANEL>, dim3(grid), dim3(MX_THREADS), (size_t)Ring<MODE_PANEL>::smem,
+                       s, prio, m->panel_a[k & 1], m->linv_b, v, pre, nt, k, kind, ctr, pexp);
+  if (kind == KIND_DCOL || kind == KIND_DREST || kind == KIND_DALL)
+    return launch_prio(slice_gemm_kernel<MODE_TRAIL_DIAG>, dim3(grid), dim3(MX_THREADS),
+                       (size_t)Ring<MODE_TRAIL_DIAG>::smem, s, prio, m->panel_a[k & 1], m->panel_b[k & 1], v, pre, nt,
+                       k, kind, ctr, pexp);
+  return launch_prio(slice_gemm_kernel<MODE_TRAIL>, dim3(grid), dim3(MX_THREADS), (size_t)Ring<MODE_TRAIL>::smem, s,
+                     prio, m->panel_a4[k & 1], m->panel_b4[k & 1], v, pre, nt, k, kind, ctr, pexp);
 }
 
 cudaError_t launch_panel_mixed(const BatchView& v, const MixedMaps* m, int k, cudaStream_t s, int prio) {
   return launch_gemm(v, m, k, KIND_PANEL, s, prio);
 }
 
+// The off-diagonal tiles (reduced pair set), then the diagonal ones (full
+// set), on the same stream.
 cudaError_t launch_trail_mixed(const BatchView& v, const MixedMaps* m, int k, int part, cudaStream_t s, int prio,
                                int max_ctas) {
   const int kind = part == TRAIL_NEXT_COL ? KIND_COL : part == TRAIL_REST ? KIND_REST : KIND_ALL;
-  return launch_gemm(v, m, k, kind, s, prio, max_ctas);
+  const int diag = part == TRAIL_NEXT_COL ? KIND_DCOL : part == TRAIL_REST ? KIND_DREST : KIND_DALL;
+  cudaError_t e = launch_gemm(v, m, k, kind, s, prio, max_ctas);
+  if (e == cudaSuccess) e = launch_gemm(v, m, k, diag, s, prio, max_ctas);
+  return e;
+}
+
+int trail_launch_count(const MixedMaps* m, int k, int part) {
+  const int kind = part == TRAIL_NEXT_COL ? KIND_COL : part == TRAIL_REST ? KIND_REST : KIND_ALL;
+  const int diag = part == TRAIL_NEXT_COL ? KIND_DCOL : part == TRAIL_REST ? KIND_DREST : KIND_DALL;
+  return (mixed_tiles_kind(m, kind, k) > 0) + (mixed_tiles_kind(m, diag, k) > 0);
 }
 
 int device_sms() { return num_sms(); }

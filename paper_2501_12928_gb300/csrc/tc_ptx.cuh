@@ -150,6 +150,9 @@ __device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t saddr) {
   d |= (uint64_t)1 << 46;                               // descriptor version (sm_100 family)
   return d;                                             // swizzle mode 0: none
 }
+// The descriptor of an operand `bytes` further on: shared-memory addresses
+// lie below 256 KB, so the 14-bit start-address field never carries.
+__device__ __forceinline__ uint64_t sdesc_add(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
 // Instruction descriptor: bf16 x bf16 -> fp32, K-major A and B, M = 128, N given.
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t negate_a, uint32_t n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (negate_a << 13) | ((n >> 3) << 17) |
