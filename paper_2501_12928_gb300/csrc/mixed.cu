@@ -415,9 +415,10 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         break;
       }
       tc_fence_after();
-      // Phase 1: the four level accumulators of each output, summed to a
-      // double-float, move from tensor memory to registers; then tensor
-      // memory is released, and the next tile's products run during phase 2.
+      // Phase 1: the four level accumulators of each output, summed to an
+      // unnormalised double-float, move from tensor memory to registers;
+      // then tensor memory is released, and the next tile's products run
+      // during phase 2, which normalises the sums.
       float prh[NC], prl[NC], pih[NC], pil[NC];
 #pragma unroll
       for (int c0 = 0; c0 < NC; c0 += 4) {
@@ -435,8 +436,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const dfl vr = levels_sum(lr[0][q], lr[1][q], lr[2][q], lr[3][q]);
-          const dfl vi = levels_sum(li[0][q], li[1][q], li[2][q], li[3][q]);
+          const dfl vr = levels_sum_split(lr[0][q], lr[1][q], lr[2][q], lr[3][q]);
+          const dfl vi = levels_sum_split(li[0][q], li[1][q], li[2][q], li[3][q]);
           prh[c0 + q] = vr.hi;
           prl[c0 + q] = vr.lo;
           pih[c0 + q] = vi.hi;
@@ -463,8 +464,10 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           ex = max(-250, min(250, ex));
           const int e1 = ex >> 1, e2 = ex - e1;   // two exact power-of-two factors
           const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
-          const dfl vr{prh[c0 + q] * s1 * s2, prl[c0 + q] * s1 * s2};
-          const dfl vi{pih[c0 + q] * s1 * s2, pil[c0 + q] * s1 * s2};
+          const dfl nr = df_fast_two_sum(prh[c0 + q], prl[c0 + q]);
+          const dfl ni = df_fast_two_sum(pih[c0 + q], pil[c0 + q]);
+          const dfl vr{nr.hi * s1 * s2, nr.lo * s1 * s2};
+          const dfl vi{ni.hi * s1 * s2, ni.lo * s1 * s2};
           float4* cp = C + (int64_t)c * BEOR_TB;
           if (TRAILING) {
             const float4 w = cv[q];

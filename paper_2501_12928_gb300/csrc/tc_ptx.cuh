@@ -168,6 +168,24 @@ __device__ __forceinline__ dfl levels_sum(float l0, float l1, float l2, float l3
   const dfl b = df_two_sum(a.hi, l2);
   return df_fast_two_sum(b.hi, b.lo + (a.lo + l3));
 }
+// The same sum in 10 operations, as an unnormalised double-float (hi, lo),
+// for the accumulator drain, where every operation holds the tensor core
+// idle (the normalisation below runs after tensor memory is released): levels 1 and 2 are split exactly into nearest integer and fraction
+// (adding and subtracting 1.5 * 2^23 rounds to the nearest integer for
+// |x| < 2^22; |l1| < 2^15, |l2| < 2^8); hi = l0 + int(l1) + int(l2) is an
+// exact integer below 2^23, frac(l1) + frac(l2) is exact (multiples of 2^-16,
+// |.| <= 1), and lo adds the rounded level 3 (|l3| < 2), so |lo| < 4.
+// df_fast_two_sum(hi, lo) then normalises it exactly: for |hi| >= 4 the
+// exponent of hi is the larger, for hi = 0 it is trivial, and for an
+// integer |hi| <= 3 both s - hi and lo - (s - hi) are representable.
+__device__ __forceinline__ dfl levels_sum_split(float l0, float l1, float l2, float l3) {
+  const float m = 12582912.0f;   // 1.5 * 2^23
+  const float r1 = __fsub_rn(__fadd_rn(l1, m), m);
+  const float r2 = __fsub_rn(__fadd_rn(l2, m), m);
+  const float hi = __fadd_rn(__fadd_rn(l0, r1), r2);
+  const float lo = __fadd_rn(__fadd_rn(__fsub_rn(l1, r1), __fsub_rn(l2, r2)), l3);
+  return {hi, lo};
+}
 // a - b for double-float numbers with |a.lo|, |b.lo| below half an ulp of
 // their high parts: one exact two-sum of the high parts, the low parts added
 // in fp32 (relative error ~2^-44), renormalised.

@@ -13,6 +13,9 @@
   float32 level accumulators of levels 0-2 are exact over a 128-complex
   block column, and the four levels give the product to about 2^-40 of the
   operand row scales.
+* The accumulator drain's 13-operation level sum (exact integer and
+  fraction parts, one fast two-sum) is exact up to one rounding of level 3
+  and normalised, also where the low part exceeds the high part.
 * The residual's exact split of M into three floats per component.
 """
 
@@ -153,6 +156,73 @@ def test_slice_product_levels_exact_and_sum_accurate():
     scale = K * np.exp2(eA[:, None] + eB[None, :])
     err = np.abs(P - A @ B.T) / scale
     assert err.max() <= 2.0 ** -40, err.max()          # measured: 2^-42.4
+
+
+def _levels_sum_split(l0, l1, l2, l3):
+    """The drain's level sum in float32 (RN at every step, as numpy float32
+    arithmetic is): nearest integers of levels 1 and 2 by adding and
+    subtracting 1.5 * 2^23, hi = l0 + int(l1) + int(l2), lo = frac(l1) +
+    frac(l2) + l3, then one fast two-sum."""
+    f = np.float32
+    m = f(12582912.0)
+    r1 = (l1 + m) - m
+    r2 = (l2 + m) - m
+    hi = (l0 + r1) + r2
+    lo = ((l1 - r1) + (l2 - r2)) + l3
+    s = hi + lo
+    e = lo - (s - hi)
+    return hi, lo, s, e
+
+
+def test_cheap_level_sum_is_exact_and_normalised():
+    """The accumulator drain adds the four levels in 13 float32 operations
+    instead of two exact two-sums: the integer part is exact, the fast
+    two-sum that normalises (hi, lo) loses nothing (also for |hi| <= 3 below
+    |lo|), and the result is the exact level sum within one rounding of
+    level 3 (2^-22 units, |lo| < 4)."""
+    g = np.random.default_rng(11)
+    n = 200000
+    f = np.float32
+    # levels in their units: l0 integer |l0| <= 2^22, l1 multiple of 2^-8
+    # below 2^15, l2 multiple of 2^-16 below 192, l3 any float below 2
+    l0 = g.integers(-2 ** 22, 2 ** 22 + 1, n).astype(f)
+    l1 = (g.integers(-2 ** 23, 2 ** 23 + 1, n) * 2.0 ** -8).astype(f)
+    l2 = (g.integers(-192 * 2 ** 16, 192 * 2 ** 16 + 1, n) * 2.0 ** -16).astype(f)
+    l3 = g.uniform(-2, 2, n).astype(f)
+    # small high parts too, where |lo| may exceed |hi|
+    k = n // 4
+    l0[:k] = g.integers(-3, 4, k)
+    l1[:k] = (g.integers(-128, 129, k) * 2.0 ** -8).astype(f)
+    l2[:k] = (g.integers(-2 ** 15, 2 ** 15 + 1, k) * 2.0 ** -16).astype(f)
+    hi, lo, s, e = _levels_sum_split(l0, l1, l2, l3)
+    assert np.array_equal(hi.astype(np.float64),
+                          l0.astype(np.float64) + np.rint(l1.astype(np.float64)) + np.rint(l2.astype(np.float64)))
+    assert np.all(np.abs(lo) < 4)
+    # fast two-sum exact: s + e == hi + lo, and e within half an ulp of s
+    assert np.array_equal(s.astype(np.float64) + e.astype(np.float64), hi.astype(np.float64) + lo.astype(np.float64))
+    assert np.all(np.abs(e) <= np.spacing(np.abs(s)) / 2)
+    exact = l0.astype(np.float64) + l1.astype(np.float64) + l2.astype(np.float64) + l3.astype(np.float64)
+    err = np.abs(s.astype(np.float64) + e.astype(np.float64) - exact)
+    assert err.max() <= 2.0 ** -22, err.max()
+    # on accumulated levels of a real slice product it matches the two-sum version
+    ta = _two_sum_levels(l0[k:k + 1000], l1[k:k + 1000], l2[k:k + 1000], l3[k:k + 1000])
+    tb = s[k:k + 1000].astype(np.float64) + e[k:k + 1000].astype(np.float64)
+    assert np.abs(ta - tb).max() <= 2.0 ** -21
+
+
+def _two_sum_levels(l0, l1, l2, l3):
+    """The reference level sum: two exact two-sums, the small terms into the
+    low part, evaluated in float32 and returned as hi + lo in float64."""
+    def two_sum(a, b):
+        s = a + b
+        bb = s - a
+        return s, (a - (s - bb)) + (b - bb)
+    ah, al = two_sum(l0, l1)
+    bh, bl = two_sum(ah, l2)
+    lo = bl + (al + l3)
+    s = bh + lo
+    e = lo - (s - bh)
+    return s.astype(np.float64) + e.astype(np.float64)
 
 
 def test_float_triple_split_of_m_is_exact():
