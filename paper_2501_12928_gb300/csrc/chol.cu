@@ -169,6 +169,71 @@ cudaError_t launch_prior_init(const BatchView& v, bool mixed, cudaStream_t s) {
 #define DG_PACK (BEOR_TB * (BEOR_TB + 1) / 2)
 __device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
 
+// Complex Dot2 accumulation of a b into c (c[0] + c[1] the real part,
+// c[2] + c[3] the imaginary part): a an element of L as double-float with
+// its third terms at, b a double-float element.
+__device__ __forceinline__ void cmac_l(dfl* c, float4 a, float2 at, float4 b) {
+  dot2_acc3(c[0], a.x, a.y, at.x, b.x, b.y);
+  dot2_acc3(c[1], -a.z, -a.w, -at.y, b.z, b.w);
+  dot2_acc3(c[2], a.x, a.y, at.x, b.z, b.w);
+  dot2_acc3(c[3], a.z, a.w, at.y, b.x, b.y);
+}
+__device__ __forceinline__ dfl df_add_quick(dfl x, dfl y) {
+  const dfl t = df_two_sum(x.hi, y.hi);
+  return dfl{t.hi, t.lo + (x.lo + y.lo)};
+}
+// Barrier of the 128 threads (four warps) of group id - 1.
+__device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+// Block row I of the diagonal block's inverse, in place (512 threads): the
+// rows 32 I .. 32 I + 31 of L (packed, double-float plus third terms Lt),
+// every earlier block row and the diagonal block Linv_II already inverted.
+// Output (J, r, c) of the block row goes to thread o % 512 (o = 1024 J +
+// 32 r + c): lanes take consecutive columns, so a warp reads one element of
+// L (a broadcast) and 32 consecutive elements of Linv per step.
+template <int I>
+__device__ __forceinline__ void inv_block_row(float4* Af, const float2* Lt, int tid) {
+  constexpr int NQ = 2 * I;   // outputs per thread
+  dfl xr[NQ], xi[NQ];
+  // X_IJ = sum_{m = 32 J + c}^{32 I - 1} L[i][m] Linv[m][jj] (Linv_JJ is lower triangular)
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int o = tid + 512 * q, J = o >> 10, r = (o >> 5) & 31, c = o & 31;
+    const int i = 32 * I + r, jj = 32 * J + c;
+    dfl a[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    for (int m = jj; m < 32 * I; ++m) cmac_l(a, Af[pk(i, m)], Lt[pk(i, m)], Af[pk(m, jj)]);
+    xr[q] = df_add_quick(a[0], a[1]);
+    xi[q] = df_add_quick(a[2], a[3]);
+  }
+  __syncthreads();   // every read of block row I (as L) is done
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int o = tid + 512 * q, J = o >> 10, r = (o >> 5) & 31, c = o & 31;
+    const dfl ur = df_fast_two_sum(xr[q].hi, xr[q].lo), ui = df_fast_two_sum(xi[q].hi, xi[q].lo);
+    Af[pk(32 * I + r, 32 * J + c)] = make_float4(ur.hi, ur.lo, ui.hi, ui.lo);
+  }
+  __syncthreads();   // X in place of L_IJ
+  // Linv_IJ = -Linv_II X_IJ = -sum_{t <= r} Linv[i][32 I + t] X[32 I + t][jj]
+  const float2 zero = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int o = tid + 512 * q, J = o >> 10, r = (o >> 5) & 31, c = o & 31;
+    const int i = 32 * I + r, jj = 32 * J + c;
+    dfl a[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    for (int t = 0; t <= r; ++t) cmac_l(a, Af[pk(i, 32 * I + t)], zero, Af[pk(32 * I + t, jj)]);
+    xr[q] = df_add_quick(a[0], a[1]);
+    xi[q] = df_add_quick(a[2], a[3]);
+  }
+  __syncthreads();   // every read of X is done
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int o = tid + 512 * q, J = o >> 10, r = (o >> 5) & 31, c = o & 31;
+    const dfl ur = df_fast_two_sum(xr[q].hi, xr[q].lo), ui = df_fast_two_sum(xi[q].hi, xi[q].lo);
+    Af[pk(32 * I + r, 32 * J + c)] = make_float4(-ur.hi, -ur.lo, -ui.hi, -ui.lo);
+  }
+  __syncthreads();
+}
+
 template <typename WS>
 __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int kg, int mixed) {
   extern __shared__ double2 dsm[];
@@ -350,60 +415,42 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int kg, int mixe
     s_invs[tid] = df_from_double(1.0 / ((double)d.x + (double)d.y + (double)Lt[pk(tid, tid)].x));
   }
   __syncthreads();
+  // Blocked inverse (four 32-row blocks): the diagonal blocks are inverted
+  // row by row, one block per 128 threads at once; then block row I = 1..3
+  // takes X_IJ = sum_{M=J}^{I-1} L_IM Linv_MJ for every J < I and
+  // Linv_IJ = -Linv_II X_IJ.  32 dependent row steps and 12 barriers instead
+  // of 128 row steps with two barriers each; the operations per element are
+  // those of the row recursion, with the division by L_ii of each step
+  // replaced by the product with the inverted diagonal block.
   {
-    // four threads share each dot product (thread = 4 jj + part); each keeps
-    // eight independent Dot2 chains (re/im x product x m parity), combined
-    // by exact two-sums, to shorten the dependent-add latency
-    const int jj = tid >> 2, part = tid & 3;
-    for (int i = 0; i < BEOR_TB; ++i) {
-      dfl c[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) c[q] = dfl{0.0f, 0.0f};
-      if (jj < i) {
-        int m = jj + part;
-        for (; m + 4 < i; m += 8) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int mm = m + 4 * h;
-            const float4 a = Af[pk(i, mm)], b = Af[pk(mm, jj)];
-            const float2 at = Lt[pk(i, mm)];
-            dot2_acc3(c[4 * h + 0], a.x, a.y, at.x, b.x, b.y);
-            dot2_acc3(c[4 * h + 1], -a.z, -a.w, -at.y, b.z, b.w);
-            dot2_acc3(c[4 * h + 2], a.x, a.y, at.x, b.z, b.w);
-            dot2_acc3(c[4 * h + 3], a.z, a.w, at.y, b.x, b.y);
-          }
-        }
-        if (m < i) {
-          const float4 a = Af[pk(i, m)], b = Af[pk(m, jj)];
-          const float2 at = Lt[pk(i, m)];
-          dot2_acc3(c[0], a.x, a.y, at.x, b.x, b.y);
-          dot2_acc3(c[1], -a.z, -a.w, -at.y, b.z, b.w);
-          dot2_acc3(c[2], a.x, a.y, at.x, b.z, b.w);
-          dot2_acc3(c[3], a.z, a.w, at.y, b.x, b.y);
-        }
-      }
-      auto add = [](dfl x, dfl y) {
-        const dfl t = df_two_sum(x.hi, y.hi);
-        return dfl{t.hi, t.lo + (x.lo + y.lo)};
-      };
-      dfl sr = add(add(c[0], c[1]), add(c[4], c[5]));
-      dfl si = add(add(c[2], c[3]), add(c[6], c[7]));
+    const int g = tid >> 7, lt = tid & 127, jl = lt >> 2, part = lt & 3;
+    const int jj = 32 * g + jl;
+    for (int il = 0; il < 32; ++il) {
+      const int i = 32 * g + il;
+      dfl c[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+      if (jl < il)
+        for (int m = jj + part; m < i; m += 4) cmac_l(c, Af[pk(i, m)], Lt[pk(i, m)], Af[pk(m, jj)]);
+      dfl sr = df_add_quick(c[0], c[1]), si = df_add_quick(c[2], c[3]);
 #pragma unroll
       for (int o = 1; o <= 2; o <<= 1) {
-        sr = add(sr, dfl{__shfl_xor_sync(0xffffffffu, sr.hi, o), __shfl_xor_sync(0xffffffffu, sr.lo, o)});
-        si = add(si, dfl{__shfl_xor_sync(0xffffffffu, si.hi, o), __shfl_xor_sync(0xffffffffu, si.lo, o)});
+        sr = df_add_quick(sr, dfl{__shfl_xor_sync(0xffffffffu, sr.hi, o), __shfl_xor_sync(0xffffffffu, sr.lo, o)});
+        si = df_add_quick(si, dfl{__shfl_xor_sync(0xffffffffu, si.hi, o), __shfl_xor_sync(0xffffffffu, si.lo, o)});
       }
-      __syncthreads();
-      if (jj < i && part == 0) {
+      group_sync(1 + g);   // every read of row i (as L) is done
+      if (jl < il && part == 0) {
         const dfl inv = s_invs[i];
         const dfl qr = df_mul(df_fast_two_sum(sr.hi, sr.lo), inv);
         const dfl qi = df_mul(df_fast_two_sum(si.hi, si.lo), inv);
         Af[pk(i, jj)] = make_float4(-qr.hi, -qr.lo, -qi.hi, -qi.lo);
       }
-      if (tid == 0) Af[pk(i, i)] = make_float4(s_invs[i].hi, s_invs[i].lo, 0.0f, 0.0f);
-      __syncthreads();
+      if (lt == 0) Af[pk(i, i)] = make_float4(s_invs[i].hi, s_invs[i].lo, 0.0f, 0.0f);
+      group_sync(1 + g);   // row i of Linv is complete
     }
   }
+  __syncthreads();
+  inv_block_row<1>(Af, Lt, tid);
+  inv_block_row<2>(Af, Lt, tid);
+  inv_block_row<3>(Af, Lt, tid);
   double2* dinv = v.dinv + pr.dinv_off + (int64_t)k * DG_PACK;
   for (int e = tid; e < DG_PACK; e += nthr) {
     const float4 f = Af[e];
