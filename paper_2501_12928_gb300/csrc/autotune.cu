@@ -6,11 +6,14 @@
 // tuner may pick any candidate on time alone.  Each candidate is applied
 // with beor_set_schedule, its batch built and its graph captured by one
 // untimed evaluation, and then timed over `reps` evaluations through the
-// public call (device time of the graph launch, beor_stats.ms_last).  The
+// public call (device time of the graph launch, beor_stats.ms_last, the
+// fastest of them); the two fastest candidates and the default are then
+// timed again, in turn, twice, and the fastest time of each decides.  The
 // result is kept in a cache file of one JSON object per line, keyed by the
 // device name and the batch shape.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -156,36 +159,65 @@ extern "C" int beor_autotune(beor_ctx* const* ctxs, int nsets, const double* con
     lp[s] = lo[s].data();
     sp[s] = so[s].data();
   }
-  double best = INFINITY, first = -1.0;
-  beor_schedule best_s = cand[0];
   int last_err = BEOR_OK;
-  for (size_t c = 0; c < cand.size(); ++c) {
-    r = beor_set_schedule(ctxs, nsets, B, &cand[c]);
-    if (r) return r;
-    r = beor_lnl_multi(ctxs, nsets, phi, B, lp.data(), sp.data(), nullptr);   // builds, captures, runs once
-    if (r == BEOR_ENOMEM) {
-      last_err = r;
-      continue;
+  // time one candidate: one untimed evaluation (builds, captures and runs
+  // the graph), then the fastest of `reps`; INFINITY if it does not fit
+  auto time_of = [&](const beor_schedule& sc, double* out) -> int {
+    *out = INFINITY;
+    int e = beor_set_schedule(ctxs, nsets, B, &sc);
+    if (e) return e;
+    e = beor_lnl_multi(ctxs, nsets, phi, B, lp.data(), sp.data(), nullptr);
+    if (e == BEOR_ENOMEM) {
+      last_err = e;
+      return BEOR_OK;
     }
-    if (r) return r;
-    double t = INFINITY;
+    if (e) return e;
     for (int i = 0; i < reps; ++i) {
-      r = beor_lnl_multi(ctxs, nsets, phi, B, lp.data(), sp.data(), nullptr);
-      if (r) return r;
+      e = beor_lnl_multi(ctxs, nsets, phi, B, lp.data(), sp.data(), nullptr);
+      if (e) return e;
       beor_stats st{};
       beor_get_stats(ctxs[0], &st);
-      if (st.ms_last > 0.0 && st.ms_last < t) t = st.ms_last;
+      if (st.ms_last > 0.0 && st.ms_last < *out) *out = st.ms_last;
     }
-    if (c == 0) first = t;
-    if (t < best) {
-      best = t;
-      best_s = cand[c];
-    }
+    return BEOR_OK;
+  };
+  std::vector<double> t1(cand.size(), INFINITY);
+  for (size_t c = 0; c < cand.size(); ++c) {
+    r = time_of(cand[c], &t1[c]);
+    if (r) return r;
   }
-  if (!std::isfinite(best)) {
+  // The candidates differ by a few per cent, about as much as the GPU's
+  // clock under its power cap drifts during the sweep: the two fastest and
+  // the default are timed again, in turn, twice, and the fastest time of
+  // each over both passes decides.
+  std::vector<size_t> order(cand.size());
+  for (size_t c = 0; c < cand.size(); ++c) order[c] = c;
+  std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return t1[a] < t1[b]; });
+  std::vector<size_t> fin;
+  for (size_t q = 0; q < order.size() && fin.size() < 2; ++q)
+    if (std::isfinite(t1[order[q]])) fin.push_back(order[q]);
+  if (fin.empty()) {
     beor_set_schedule(ctxs, nsets, B, &cur);
     return last_err ? last_err : BEOR_ECUDA;
   }
+  if (std::find(fin.begin(), fin.end(), (size_t)0) == fin.end() && std::isfinite(t1[0])) fin.push_back(0);
+  std::vector<double> t2(fin.size(), INFINITY);
+  for (int pass = 0; pass < 2 && fin.size() > 1; ++pass)
+    for (size_t q = 0; q < fin.size(); ++q) {
+      double t = INFINITY;
+      r = time_of(cand[fin[q]], &t);
+      if (r) return r;
+      t2[q] = std::min(t2[q], t);
+    }
+  if (fin.size() == 1) t2[0] = t1[fin[0]];
+  size_t bq = 0;
+  for (size_t q = 1; q < fin.size(); ++q)
+    if (t2[q] < t2[bq]) bq = q;
+  const double best = t2[bq];
+  const beor_schedule best_s = cand[fin[bq]];
+  double first = t1[0];
+  for (size_t q = 0; q < fin.size(); ++q)
+    if (fin[q] == 0) first = t2[q];
   r = beor_set_schedule(ctxs, nsets, B, &best_s);
   if (r) return r;
   if (cache_path) write_entry(cache_path, dev, key, best_s, best, first);
