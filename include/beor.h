@@ -303,9 +303,10 @@ int beor_get_schedule(beor_ctx *const *ctxs, int n_sets, const int *B, beor_sche
  * Otherwise every candidate -- look-ahead on with rest_ctas in {one per SM,
  * 8, 16, 24 fewer}, align_ends in {1, 0} and reserve_diag in {0, 1}, and
  * look-ahead off with align_ends in {1, 0} -- is applied and timed: one
- * untimed evaluation
- * (building the batch and its graph), then `reps` evaluations (1..100),
- * the fastest device time counting.  The fastest candidate is applied
+ * untimed evaluation (building the batch and its graph), then `reps`
+ * evaluations (1..100), the fastest device time counting; the two fastest
+ * and the default are then timed again, in turn, twice.  The fastest
+ * candidate is applied
  * (beor_set_schedule) and, with cache_path, appended to the cache (one JSON
  * object per line).  chosen, ms_chosen (its time per evaluation) and
  * ms_default (the default schedule's time, -1 when read from the cache
