@@ -12,7 +12,11 @@
 // pairs (0,2), (1,1), (2,0) (at most 1.26e7 units of 2^-16).  All pairs with
 // s + t >= 3 share a fourth accumulator whose rounding error (about 2^-19 of
 // its size after ~1500 fp32 additions) lies about 2^-39 below the leading
-// term.  The epilogue adds the four levels as a double-float number,
+// term.  The off-diagonal tiles of the trailing update take the reduced pair
+// set (s + t <= 3 and (2, 2): the pairs dropped lie 2^-32 below the leading
+// term and have no sign bias there); its diagonal tiles and the panel
+// product take all pairs with s + t <= 4.  The epilogue adds the four
+// levels as a double-float number,
 // scales by 2^(e_r + e_c - 14) and updates the working matrix, itself kept as
 // a double-float pair per real number.  The result is accurate to about
 // 2^-40 of the operand row scales, which keeps log|Sigma| well inside the
@@ -26,9 +30,10 @@
 // products of one A part with a two-part window of B: Im A times the window
 // (Im B, Re B) adds (Ai Bi, Ai Br) to (re, im), and Re A times (Re B, -Im B)
 // adds (Ar Br, -Ar Bi), so one MMA covers the real and imaginary outputs of
-// up to two levels (N up to 256): 11 MMAs per A part and K-chunk instead of
-// 18 with separate re / im accumulators, which cuts the tensor cores' reads
-// of A from shared memory by 40 %.  The slice planes hold the parts
+// up to two levels (N up to 256): 11 MMAs per A part and K-chunk for the
+// full pair set (7 for the reduced one) instead of 18 with separate re / im
+// accumulators, which cuts the tensor cores' reads of A from shared memory
+// by 40 %.  The slice planes hold the parts
 // (Im, Re, -Im) of each slice for that reason.  Warp 0 issues TMA loads into
 // a shared-memory ring of half-stages (one A part of 128 rows and its B
 // window of 64 rows, one K-chunk of 16), fetched from the planes stored in
