@@ -502,97 +502,126 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 // ---------------------------------------------------------------------------
 // slicing of the panel rows: rows of tiles (i, k), i > k, of every problem
 // ---------------------------------------------------------------------------
+constexpr int SL_R = 16;                                    // rows per group
+constexpr int SL_GROUPS = 4;                                // groups per CTA (half a block row)
+constexpr int SL_CTAS = BEOR_TB / (SL_R * SL_GROUPS);       // CTAs per block row
+constexpr int SL_BUF = BEOR_TB * (SL_R + 1);                // float4 per buffer: [column][row], padded
+constexpr int SL_SMEM = 2 * SL_BUF * (int)sizeof(float4);   // double buffer: 69632 bytes
+
+__device__ __forceinline__ void cp_async16(float4* dst, const float4* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// Two CTAs per block row i of every problem, each taking four groups of 16
+// rows in turn: the next group's double-float rows are copied into shared
+// memory (cp.async) while the current group is sliced.
 __global__ void __launch_bounds__(256)
     slice_panel_kernel(BatchView v, int kg, __nv_bfloat16* __restrict__ panel_sl, int32_t* __restrict__ panel_exp) {
-  constexpr int R = 16;                     // rows per block
-  __shared__ float4 s[BEOR_TB][R + 1];      // [column][row], padded
+  extern __shared__ float4 sl_smem[];
+  __shared__ int s_e[SL_R];
   const int p = blockIdx.y;
   const Prob pr = v.prob[p];
   const int k = kg - pr.k_off;   // this problem's block step
-  const int i = k + 1 + blockIdx.x / (BEOR_TB / R);
+  const int i = k + 1 + blockIdx.x / SL_CTAS;
+  const int g0 = (blockIdx.x % SL_CTAS) * SL_GROUPS;   // first group of this CTA
   if (k < 0 || i >= pr.nt || prob_skipped(v.status[p])) return;
-  const int r0 = (blockIdx.x % (BEOR_TB / R)) * R;
   if (!BEOR_INBOUNDS(v.flags, pr.ws_off + (tri_index(i, k) + 1) * BEOR_TILE_ELEMS <= v.ws_elems, BC_SLICE_ROW)) return;
   const float4* tile = reinterpret_cast<const float4*>(v.ws) + pr.ws_off + tri_index(i, k) * BEOR_TILE_ELEMS;
-  for (int e = threadIdx.x; e < BEOR_TB * R; e += 256) {
-    int c = e / R, r = e % R;
-    s[c][r] = tile[c * BEOR_TB + r0 + r];
-  }
-  __syncthreads();
+  auto load_group = [&](int grp) {   // rows 16 (g0 + grp) .. + 15, every column
+    float4* buf = sl_smem + (grp & 1) * SL_BUF;
+    for (int e = threadIdx.x; e < BEOR_TB * SL_R; e += 256) {
+      const int c = e / SL_R, r = e % SL_R;
+      cp_async16(buf + c * (SL_R + 1) + r, tile + c * BEOR_TB + (g0 + grp) * SL_R + r);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t rows = v.rows;
-  __shared__ int s_e[R];
-  // per-row exponent (one warp per row)
-  for (int r = warp; r < R; r += 8) {
-    float mx = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float4 a = s[lane + 32 * q][r];
-      mx = fmaxf(mx, fmaxf(fabsf(a.x), fabsf(a.z)));
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int e = mx > 0.0f ? ilogbf(mx) + 1 : -1000;
-    if (lane == 0) {
-      s_e[r] = e;
-      if (BEOR_INBOUNDS(v.flags, pr.row_off + (int64_t)i * BEOR_TB + r0 + r < rows, BC_SLICE_ROW))
-        panel_exp[pr.row_off + (int64_t)i * BEOR_TB + r0 + r] = e;
-    }
-  }
-  __syncthreads();
-  // Digits.  Each thread makes one 16-byte chunk of every plane: one row and
-  // 8 consecutive columns.  Warp w takes K-chunk w and lane = (8-row group,
-  // K half, row), so that a warp writes 512 contiguous bytes of each plane.
-  static_assert(R == 16 && BEOR_TB / MX_KC == 8, "one warp per K-chunk, 32 chunks of 16 bytes per warp");
-  const int rr = lane & 7, kh = (lane >> 3) & 1, g = lane >> 4;
-  const int r = g * 8 + rr;
+  // digit work: one 16-byte chunk of every plane per thread (one row, 8
+  // consecutive columns); warp w takes K-chunk w and lane = (8-row group, K
+  // half, row), so that a warp writes 512 contiguous bytes of each plane
+  static_assert(SL_R == 16 && BEOR_TB / MX_KC == 8, "one warp per K-chunk, 32 chunks of 16 bytes per warp");
+  const int rr = lane & 7, kh = (lane >> 3) & 1, hg = lane >> 4;
+  const int r = hg * 8 + rr;
   const int c0 = warp * MX_KC + kh * 8;
-  const int e = s_e[r];
-  const int64_t grow = pr.row_off + (int64_t)i * BEOR_TB + r0 + r;
-  uint32_t packed[BEOR_NPLANE][4];
+  load_group(0);
+  for (int grp = 0; grp < SL_GROUPS; ++grp) {
+    if (grp + 1 < SL_GROUPS) {
+      load_group(grp + 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();   // group grp is in shared memory
+    const float4* buf = sl_smem + (grp & 1) * SL_BUF;
+    const int r0 = (g0 + grp) * SL_R;
+    // per-row exponent (one warp per row)
+    for (int rw = warp; rw < SL_R; rw += 8) {
+      float mx = 0.0f;
 #pragma unroll
-  for (int q = 0; q < 8; q += 2) {
-    float val[2][BEOR_NPLANE];
+      for (int q = 0; q < 4; ++q) {
+        const float4 a = buf[(lane + 32 * q) * (SL_R + 1) + rw];
+        mx = fmaxf(mx, fmaxf(fabsf(a.x), fabsf(a.z)));
+      }
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const int e = mx > 0.0f ? ilogbf(mx) + 1 : -1000;
+      if (lane == 0) {
+        s_e[rw] = e;
+        if (BEOR_INBOUNDS(v.flags, pr.row_off + (int64_t)i * BEOR_TB + r0 + rw < rows, BC_SLICE_ROW))
+          panel_exp[pr.row_off + (int64_t)i * BEOR_TB + r0 + rw] = e;
+      }
+    }
+    __syncthreads();
+    const int e = s_e[r];
+    const int64_t grow = pr.row_off + (int64_t)i * BEOR_TB + r0 + r;
+    uint32_t packed[BEOR_NPLANE][4];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const float4 a = s[c0 + q + u][r];
+    for (int q = 0; q < 8; q += 2) {
+      float val[2][BEOR_NPLANE];
 #pragma unroll
-      for (int part = 0; part < 2; ++part) {   // 0: real, 1: imaginary
-        const float hi = part ? a.z : a.x, lo = part ? a.w : a.y;
-        // balanced base-256 digits of the fixed-point number round(x * 2^(39 - e))
-        long long X = 0;
-        if (e > -1000) X = round_df(ldexpf(hi, 39 - e), ldexpf(lo, 39 - e));
-        int dg[BEOR_NSLICE];
+      for (int u = 0; u < 2; ++u) {
+        const float4 a = buf[(c0 + q + u) * (SL_R + 1) + r];
 #pragma unroll
-        for (int sl = BEOR_NSLICE - 1; sl >= 1; --sl) {
-          const long long m = ((X + 128) & 255) - 128;
-          dg[sl] = (int)m;
-          X = (X - m) >> 8;
-        }
-        dg[0] = (int)X;
+        for (int part = 0; part < 2; ++part) {   // 0: real, 1: imaginary
+          const float hi = part ? a.z : a.x, lo = part ? a.w : a.y;
+          // balanced base-256 digits of the fixed-point number round(x * 2^(39 - e))
+          long long X = 0;
+          if (e > -1000) X = round_df(ldexpf(hi, 39 - e), ldexpf(lo, 39 - e));
+          int dg[BEOR_NSLICE];
 #pragma unroll
-        for (int sl = 0; sl < BEOR_NSLICE; ++sl) {
-          const float d = ldexpf((float)dg[sl], -8 * sl);
-          if (part == 0) {
-            val[u][slice_plane(sl, BEOR_PART_RE)] = d;
-          } else {
-            val[u][slice_plane(sl, BEOR_PART_IM)] = d;
-            val[u][slice_plane(sl, BEOR_PART_NEGIM)] = -d;
+          for (int sl = BEOR_NSLICE - 1; sl >= 1; --sl) {
+            const long long m = ((X + 128) & 255) - 128;
+            dg[sl] = (int)m;
+            X = (X - m) >> 8;
+          }
+          dg[0] = (int)X;
+#pragma unroll
+          for (int sl = 0; sl < BEOR_NSLICE; ++sl) {
+            const float d = ldexpf((float)dg[sl], -8 * sl);
+            if (part == 0) {
+              val[u][slice_plane(sl, BEOR_PART_RE)] = d;
+            } else {
+              val[u][slice_plane(sl, BEOR_PART_IM)] = d;
+              val[u][slice_plane(sl, BEOR_PART_NEGIM)] = -d;
+            }
           }
         }
       }
-    }
 #pragma unroll
-    for (int pl = 0; pl < BEOR_NPLANE; ++pl) {
-      const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[0][pl], val[1][pl]);   // .x at the lower address
-      packed[pl][q / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+      for (int pl = 0; pl < BEOR_NPLANE; ++pl) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[0][pl], val[1][pl]);   // .x at the lower address
+        packed[pl][q / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
     }
+    const int64_t off = slice_elem_off(grow, c0, rows);   // a multiple of 8 elements: 16-byte aligned
+    if (BEOR_INBOUNDS(v.flags, grow < rows && off + 8 <= rows * BEOR_TB, BC_SLICE_OFF)) {
+#pragma unroll
+      for (int pl = 0; pl < BEOR_NPLANE; ++pl)
+        *reinterpret_cast<uint4*>(panel_sl + (int64_t)pl * rows * BEOR_TB + off) =
+            make_uint4(packed[pl][0], packed[pl][1], packed[pl][2], packed[pl][3]);
+    }
+    __syncthreads();   // buffer grp & 1 and s_e may be overwritten
   }
-  const int64_t off = slice_elem_off(grow, c0, rows);   // a multiple of 8 elements: 16-byte aligned
-  if (!BEOR_INBOUNDS(v.flags, grow < rows && off + 8 <= rows * BEOR_TB, BC_SLICE_OFF)) return;
-#pragma unroll
-  for (int pl = 0; pl < BEOR_NPLANE; ++pl)
-    *reinterpret_cast<uint4*>(panel_sl + (int64_t)pl * rows * BEOR_TB + off) =
-        make_uint4(packed[pl][0], packed[pl][1], packed[pl][2], packed[pl][3]);
 }
 
 static __nv_bfloat16* slice_buf(const BatchView& v, int k) {
@@ -601,10 +630,15 @@ static __nv_bfloat16* slice_buf(const BatchView& v, int k) {
 static int32_t* exp_buf(const BatchView& v, int k) { return v.panel_exp + (size_t)(k & 1) * v.rows; }
 
 cudaError_t launch_slice_panel(const BatchView& v, int k, cudaStream_t s, int prio) {
-  const int nblk = 8 * (v.max_nt - 1 - k);
+  const int nblk = SL_CTAS * (v.max_nt - 1 - k);   // block rows below block column k
   if (nblk <= 0) return cudaSuccess;
-  return launch_prio(slice_panel_kernel, dim3(nblk, v.P), dim3(256), 0, s, prio, v, k, slice_buf(v, k),
-                     exp_buf(v, k));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(slice_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SL_SMEM);
+    attr = true;
+  }
+  return launch_prio(slice_panel_kernel, dim3(nblk, v.P), dim3(256), (size_t)SL_SMEM, s, prio, v, k,
+                     slice_buf(v, k), exp_buf(v, k));
 }
 
 // ---------------------------------------------------------------------------
