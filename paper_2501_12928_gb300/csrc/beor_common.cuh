@@ -224,17 +224,50 @@ __device__ __forceinline__ void dot2_acc3(dfl& acc, float ah, float al, float at
   acc.hi = s;
 }
 
-// round(a + b) to the nearest integer for a double-float a + b (|b| at most
-// half an ulp of a, |a + b| < 2^62): each part is rounded, and the sum of
-// the two residuals (each exact in fp32, within [-1/2, 1/2]) decides a
-// final step of one.  fp32 and integer operations only.
-__device__ __forceinline__ long long round_df(float a, float b) {
-  const float ra = rintf(a), rb = rintf(b);
-  long long x = (long long)ra + (long long)rb;
-  const float d = (a - ra) + (b - rb);
-  if (d > 0.5f) ++x;
-  else if (d < -0.5f) --x;
-  return x;
+// The five balanced base-256 digits of X = round((hi + lo) 2^(39 - e)) (a
+// double-float with |hi + lo| < 2^e and lo at most half an ulp of hi;
+// e <= -1000: all zero), returned as the values sigma_s 2^(-8 s) that the
+// slice planes store (exact in bf16): sigma_4 .. sigma_1 in [-128, 127]
+// taken from the bottom, sigma_0 the rest (|sigma_0| <= 128).  fp32 and
+// 32-bit integer operations only, and no conversion instructions (they run
+// on the FP64 pipe): with A, B the scaled parts (exact), A = 2^17 Ah + Al
+// with Ah = rint(A 2^-17) (|Ah| < 2^22) and Al exact; round(Al + B) is the
+// sum of the two parts' nearest integers, corrected by one step that the sum
+// of their exact residuals decides; X = 2^17 Ah + xl.  Nearest integers of
+// values below 2^22 and the digits' float values come from adding
+// 1.5 * 2^23 (whose float bits then hold the integer in the low word).
+__device__ __forceinline__ void balanced_digits5(float hi, float lo, int e, float* dv) {
+  if (e <= -1000) {
+#pragma unroll
+    for (int sl = 0; sl < BEOR_NSLICE; ++sl) dv[sl] = 0.0f;
+    return;
+  }
+  const float magic = 12582912.0f;   // 1.5 * 2^23, float bits 0x4B400000
+  const int k = 39 - e, k1 = k >> 1, k2 = k - k1;   // 2^k as two exact factors
+  const float f1 = __int_as_float((k1 + 127) << 23), f2 = __int_as_float((k2 + 127) << 23);
+  const float A = __fmul_rn(__fmul_rn(hi, f1), f2), B = __fmul_rn(__fmul_rn(lo, f1), f2);
+  const float t1 = __fmaf_rn(A, 0x1p-17f, magic);
+  const int ah = __float_as_int(t1) - 0x4B400000;
+  const float al = __fmaf_rn(-__fsub_rn(t1, magic), 131072.0f, A);   // A - 2^17 Ah, exact
+  const float t2 = __fadd_rn(al, magic), t3 = __fadd_rn(B, magic);
+  const float d = __fadd_rn(__fsub_rn(al, __fsub_rn(t2, magic)), __fsub_rn(B, __fsub_rn(t3, magic)));
+  const int xl = (__float_as_int(t2) - 0x4B400000) + (__float_as_int(t3) - 0x4B400000) + (d > 0.5f ? 1 : 0) -
+                 (d < -0.5f ? 1 : 0);
+  // digits from the bottom: X mod 256 is xl mod 256, and after two digits
+  // the rest fits 32 bits
+  int dg[BEOR_NSLICE];
+  dg[4] = ((xl + 128) & 255) - 128;
+  const int y = (xl - dg[4]) >> 8;
+  dg[3] = ((y + 128) & 255) - 128;
+  int x = 2 * ah + ((y - dg[3]) >> 8);
+  dg[2] = ((x + 128) & 255) - 128;
+  x = (x - dg[2]) >> 8;
+  dg[1] = ((x + 128) & 255) - 128;
+  dg[0] = (x - dg[1]) >> 8;
+#pragma unroll
+  for (int sl = 0; sl < BEOR_NSLICE; ++sl)
+    dv[sl] = __fmul_rn(__fsub_rn(__int_as_float(dg[sl] + 0x4B400000), magic),
+                       __int_as_float((127 - 8 * sl) << 23));
 }
 
 }  // namespace beor

@@ -476,20 +476,12 @@ __global__ void __launch_bounds__(512) diag_kernel(BatchView v, int kg, int mixe
 #pragma unroll
       for (int part = 0; part < 2; ++part) {
         const float hi = part ? a.z : a.x, lo = part ? a.w : a.y;
-        long long X = 0;
-        if (e > -1000) X = round_df(ldexpf(hi, 39 - e), ldexpf(lo, 39 - e));
-        int dg[BEOR_NSLICE];
-#pragma unroll
-        for (int sl = BEOR_NSLICE - 1; sl >= 1; --sl) {
-          const long long mm = ((X + 128) & 255) - 128;
-          dg[sl] = (int)mm;
-          X = (X - mm) >> 8;
-        }
-        dg[0] = (int)X;
+        float dv[BEOR_NSLICE];
+        balanced_digits5(hi, lo, e, dv);
         __nv_bfloat16* dst = v.linv_sl + slice_elem_off(row, m, lrows);
 #pragma unroll
         for (int sl = 0; sl < BEOR_NSLICE; ++sl) {
-          const float d = ldexpf((float)dg[sl], -8 * sl);
+          const float d = dv[sl];
           if (part == 0) {
             dst[slice_plane(sl, BEOR_PART_RE) * ps] = __float2bfloat16_rn(d);
           } else {

@@ -585,19 +585,11 @@ __global__ void __launch_bounds__(256)
         for (int part = 0; part < 2; ++part) {   // 0: real, 1: imaginary
           const float hi = part ? a.z : a.x, lo = part ? a.w : a.y;
           // balanced base-256 digits of the fixed-point number round(x * 2^(39 - e))
-          long long X = 0;
-          if (e > -1000) X = round_df(ldexpf(hi, 39 - e), ldexpf(lo, 39 - e));
-          int dg[BEOR_NSLICE];
-#pragma unroll
-          for (int sl = BEOR_NSLICE - 1; sl >= 1; --sl) {
-            const long long m = ((X + 128) & 255) - 128;
-            dg[sl] = (int)m;
-            X = (X - m) >> 8;
-          }
-          dg[0] = (int)X;
+          float dv[BEOR_NSLICE];
+          balanced_digits5(hi, lo, e, dv);
 #pragma unroll
           for (int sl = 0; sl < BEOR_NSLICE; ++sl) {
-            const float d = ldexpf((float)dg[sl], -8 * sl);
+            const float d = dv[sl];
             if (part == 0) {
               val[u][slice_plane(sl, BEOR_PART_RE)] = d;
             } else {

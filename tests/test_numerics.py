@@ -5,7 +5,8 @@
   q = dbar^H x~ + x~^H r + r^H Sigma^-1 r exactly.
 * Exact round-to-nearest of a double-float value hi + lo with float32
   operations only (each part rounded, one correction from the two exact
-  residuals), as the bf16 slicing does.
+  residuals), and the slicing kernels' conversion-free digit extraction,
+  which gives the same digits.
 * Dot2 (Ogita, Rump and Oishi 2005) in float32 reaches about twice the
   working precision, as the solves and the residual rely on.
 * The bf16 slicing: five balanced base-256 digits reconstruct any
@@ -45,6 +46,8 @@ def test_corrected_quadratic_form_identity():
 
 
 def _round_df(a, b):
+    """round(a + b) for float32 a + b: each part rounded, one correction step
+    decided by the sum of the two exact residuals (float32)."""
     a, b = np.float32(a), np.float32(b)
     ra, rb = np.rint(a), np.rint(b)
     x = np.int64(ra) + np.int64(rb)
@@ -63,6 +66,68 @@ def test_round_df_is_exact_round_to_nearest():
         ref = np.rint(exact[:2000]).astype(np.int64)
         frac = np.abs(exact[:2000] - np.floor(exact[:2000]) - 0.5)
         assert np.all((got == ref) | (frac == 0)), e
+
+
+def _digits_bottom_up(X):
+    """Balanced base-256 digits of int64 X: four from the bottom in
+    [-128, 127], the rest on top."""
+    d = [None] * 5
+    for s in range(4, 0, -1):
+        m = ((X + 128) & 255) - 128
+        d[s] = m
+        X = (X - m) >> 8
+    d[0] = X
+    return d
+
+
+def _balanced_digits5_emulated(hi, lo, e):
+    """The slicing kernels' digit extraction without conversion instructions:
+    A = 2^17 Ah + Al with Ah = rint(A 2^-17), round(Al + B) as the parts'
+    nearest integers plus one correction, then 32-bit digit arithmetic."""
+    f = np.float32
+    k = (39 - e).astype(np.int64)
+    k1 = k >> 1
+    A = (hi * np.exp2(k1).astype(f)) * np.exp2(k - k1).astype(f)
+    B = (lo * np.exp2(k1).astype(f)) * np.exp2(k - k1).astype(f)
+    ah = np.rint(A.astype(np.float64) * 2.0 ** -17)                 # magic-number rounding (RN-even)
+    al = (A.astype(np.float64) - ah * 2.0 ** 17).astype(f)          # exact
+    ra, rb = np.rint(al), np.rint(B)
+    d = (al - ra) + (B - rb)
+    xl = ra.astype(np.int64) + rb.astype(np.int64) + (d > 0.5) - (d < -0.5)
+    ah = ah.astype(np.int64)
+    d4 = ((xl + 128) & 255) - 128
+    y = (xl - d4) >> 8
+    d3 = ((y + 128) & 255) - 128
+    x = 2 * ah + ((y - d3) >> 8)
+    assert np.all(np.abs(x) < 2 ** 31)
+    d2 = ((x + 128) & 255) - 128
+    x = (x - d2) >> 8
+    d1 = ((x + 128) & 255) - 128
+    return [(x - d1) >> 8, d1, d2, d3, d4]
+
+
+def test_conversion_free_digits_match_the_64_bit_rounding():
+    """The slicing kernels' digits from fp32 and 32-bit integer operations
+    equal those of the 64-bit route (round the scaled double-float to an
+    int64 with _round_df, split it from the bottom), over exponents with
+    headroom, tiny and large values, and ties; all digits within [-128, 128]."""
+    g = np.random.default_rng(17)
+    n = 100000
+    f = np.float32
+    x = g.standard_normal(n) * np.exp(g.uniform(-40, 40, n))
+    x[:2000] = np.ldexp(np.round(g.uniform(-1, 1, 2000) * 2 ** 30), -30)   # on a coarse grid: ties
+    hi = x.astype(f)
+    lo = (x - hi.astype(np.float64)).astype(f)
+    e = (np.floor(np.log2(np.abs(hi.astype(np.float64)))) + 1 + g.integers(0, 40, n) * (g.random(n) < 0.3)).astype(np.int64)
+    got = _balanced_digits5_emulated(hi, lo, e)
+    k = 39 - e
+    A = (hi.astype(np.float64) * np.exp2(k)).astype(f)
+    B = (lo.astype(np.float64) * np.exp2(k)).astype(f)
+    X = np.array([_round_df(a, b) for a, b in zip(A, B)], dtype=np.int64)
+    ref = _digits_bottom_up(X)
+    for s in range(5):
+        np.testing.assert_array_equal(got[s], ref[s])
+    assert all(np.abs(di).max() <= 128 for di in got)
 
 
 def _dot2_f32(x, y):
