@@ -18,6 +18,8 @@
   fraction parts, one fast two-sum) is exact up to one rounding of level 3
   and normalised, also where the low part exceeds the high part.
 * The residual's exact split of M into three floats per component.
+* The blocked recurrence of the diagonal blocks' inverse (four 32 x 32
+  diagonal blocks, then block rows as block products).
 """
 
 import numpy as np
@@ -288,6 +290,34 @@ def _two_sum_levels(l0, l1, l2, l3):
     s = bh + lo
     e = lo - (s - bh)
     return s.astype(np.float64) + e.astype(np.float64)
+
+
+def test_blocked_triangular_inverse_recurrence():
+    """The diagonal-block kernel's inverse of L (128 x 128, lower): the four
+    32 x 32 diagonal blocks inverted by the row recursion, then block row
+    I = 1..3 as Linv_IJ = -Linv_II sum_{M=J}^{I-1} L_IM Linv_MJ; in float64
+    it equals the inverse to rounding."""
+    g = np.random.default_rng(5)
+    n, b = 128, 32
+    L = np.tril(g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))) * 0.1
+    L[np.diag_indices(n)] = np.abs(g.standard_normal(n)) + 1.0
+    X = np.zeros_like(L)
+    for I in range(4):   # diagonal blocks, row by row
+        s = slice(b * I, b * I + b)
+        Lb, Xb = L[s, s], np.zeros((b, b), complex)
+        for i in range(b):
+            Xb[i, i] = 1.0 / Lb[i, i]
+            for j in range(i):
+                Xb[i, j] = -(Lb[i, j:i] @ Xb[j:i, j]) / Lb[i, i]
+        X[s, s] = Xb
+    for I in range(1, 4):
+        rI = slice(b * I, b * I + b)
+        for J in range(I):
+            rJ = slice(b * J, b * J + b)
+            acc = sum(L[rI, b * M:b * M + b] @ X[b * M:b * M + b, rJ] for M in range(J, I))
+            X[rI, rJ] = -X[rI, rI] @ acc
+    ref = np.linalg.inv(L)
+    assert np.abs(X - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
 def test_float_triple_split_of_m_is_exact():
